@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark: 1080p virtual views/s of the VINet forward on B300.
+
+Workload (one step): one camera pair at 1920x1080 (padded to 1920x1088), 7
+virtual views at t = k/8, k = 1..7, through fvv_interp_run (inputs resident in
+HBM, views written to HBM).  Synthetic layered-plane scene, seeded He-init
+weights.  L2 is flushed (256 MB write) between timed steps, outside the events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+    python bench.py --impl reference ...   # the FP64 CPU oracle arm
+
+Under torchrun every rank runs its own pair (weak scaling, no collective); the
+value is all ranks' views over the slowest rank's time.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W = 1080, 1920
+TS = [k / 8 for k in range(1, 8)]
+METRIC = "1080p virtual views/s"
+SCENE_SEED, WEIGHT_SEED, MAX_DISP = 2, 0, 64.0
+FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.file = index, None, None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+        self.file.flush()
+
+    def summary(self):
+        rows = []
+        for line in open(self.file.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "power_w_max": max((num(r[3]) or 0) for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10 * np.log10(1 / mse)
+
+
+def oracle_sample(left, right, blob):
+    """One view (t = 0.5) of the workload on the host cores with the FP64 oracle."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.vinet_forward(blob, left, right, 0.5)
+    return ref, time.perf_counter() - t0, oracle.threads()
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle, timed as it stands; each step = one view of a
+    1/16-pixel sample (480x272) of the workload, scaled to 1080p views by the
+    padded pixel ratio (every layer's work is proportional to the pixel count)."""
+    if rank != 0:
+        return
+    import oracle
+    from synth import scene, weights
+    blob = weights.he_init(WEIGHT_SEED)
+    h, w = 272, 480
+    left, right = scene.stereo_pair(SCENE_SEED, h, w, MAX_DISP / 4)
+    scale = (h * w) / (1088 * 1920)
+    for _ in range(args.warmup):
+        oracle.vinet_forward(blob, left, right, 0.5)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.vinet_forward(blob, left, right, 0.5)
+    dt = time.perf_counter() - t0
+    value = args.steps * scale / dt
+    sample = f"one 480x272 view (t=0.5) per step = 1/16 of a padded 1080p view's pixels; scaled by 1/16"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic layered-plane scene, seeded He-init weights",
+            "config": config_dict(args),
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": "1 camera pair 1920x1080 (padded 1920x1088), 7 views t=k/8 per step",
+            "H": H, "W": W, "views_per_step": len(TS), "precision": args.precision,
+            "l2": "flushed between steps (256 MB write outside the timed events)",
+            "parallelism": f"replicas x{args.gpus} (independent pairs, no collective)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_2112_10603_b300 as fvv
+    from paper_2112_10603_b300 import build as fvv_build
+    from synth import scene, weights
+
+    fvv_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    blob = weights.he_init(WEIGHT_SEED)
+    left, right = scene.stereo_pair(SCENE_SEED + rank, H, W, MAX_DISP)
+    L = torch.from_numpy(left).cuda()
+    R = torch.from_numpy(right).cuda()
+    prec = {"bf16": fvv.FVV_BF16, "fp32": fvv.FVV_FP32}[args.precision]
+    try:
+        it = fvv.Interpolator(blob, H, W, precision=prec, max_views=len(TS))
+    except fvv.FvvError as e:
+        if prec != fvv.FVV_FP32:
+            print(f"bench: precision {args.precision} unavailable ({e}); using fp32", file=sys.stderr)
+            args.precision, prec = "fp32", fvv.FVV_FP32
+            it = fvv.Interpolator(blob, H, W, precision=prec, max_views=len(TS))
+        else:
+            raise
+    out = torch.empty((len(TS), H, W, 3), device="cuda")
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(interp, n, profile=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        if profile:
+            fvv.fvv_interp_profile(interp.h, True)
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            interp.run(L, R, TS, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    for _ in range(args.warmup):
+        it.run(L, R, TS, out=out)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms_total = timed_steps(it, args.steps, profile=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.summary()
+    launches = it.last_launches * args.steps
+    lms, lfl, lln = fvv.fvv_interp_layer_stats(it.h)
+    fvv.fvv_interp_profile(it.h, False)
+    t_max = ms_total
+    if dist:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    views = len(TS) * args.steps * world
+    value = views / (t_max / 1e3)
+
+    # end to end through the host-buffer call: pinned inputs in, views out, copies timed
+    pin_l = torch.from_numpy(left).pin_memory()
+    pin_r = torch.from_numpy(right).pin_memory()
+    pin_o = torch.empty((len(TS), H, W, 3), dtype=torch.float32).pin_memory()
+    t_np = np.asarray(TS, np.float32)
+    e2e_steps = max(3, min(args.steps, 5))
+    fvv.fvv_interp_run_host(it.h, pin_l, pin_r, t_np, len(TS), pin_o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fvv.fvv_interp_run_host(it.h, pin_l, pin_r, t_np, len(TS), pin_o)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": len(TS) * world / e2e_s, "unit": "views/s",
+           "h2d_bytes_per_step": 2 * left.nbytes, "d2h_bytes_per_step": len(TS) * left.nbytes}
+
+    # roofline of the dominant kernel (the convolution kernel family)
+    pk, pk_kind = peaks()
+    conv_ms, conv_fl = float(lms.sum()), float(lfl.sum())
+    if args.precision == "fp32":
+        roof = {"bound": "alu", "kernel": "conv_simt_kernel (FP32 FFMA implicit GEMM)",
+                "achieved": conv_fl / (conv_ms / 1e3) / 1e12, "peak": FP32_FFMA_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    else:
+        roof = {"bound": "tensor", "kernel": "conv_tc_kernel (tcgen05 BF16 implicit GEMM)",
+                "achieved": conv_fl / (conv_ms / 1e3) / 1e12, "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["conv_share_of_step"] = conv_ms / ms_total
+    roof["launches"] = int(lln.sum())
+
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "bf16", "fp32": "f32"}[args.precision],
+            "data": "synthetic layered-plane stereo scene (seeded), seeded He-init weights",
+            "config": config_dict(args), "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roof}
+
+    # plain FP32 path beside it, and parity vs the FP64 oracle (rank 0)
+    if rank == 0:
+        out_main = out.cpu().numpy()
+        if args.precision != "fp32":
+            it32 = fvv.Interpolator(blob, H, W, precision=fvv.FVV_FP32, max_views=len(TS))
+            it32.run(L, R, TS, out=out)
+            torch.cuda.synchronize()
+            ms32 = timed_steps(it32, args.fp32_steps)
+            line["fp32_views_per_s"] = len(TS) * args.fp32_steps / (ms32 / 1e3)
+            out32 = out.cpu().numpy()
+            it32.close()
+        else:
+            line["fp32_views_per_s"] = value / world
+            out32 = out_main
+        if not args.no_cpu_baseline:
+            ref, secs, cores = oracle_sample(left, right, blob)
+            line["cpu_baseline"] = {"value": 1.0 / secs, "unit": "views/s", "cores": cores, "kind": "oracle",
+                                    "sample": "one full 1080p view (t=0.5) of the workload"}
+            mid = TS.index(0.5)
+            line["parity"] = {
+                f"{args.precision}_vs_fp64": {"max_abs_err": float(np.abs(out_main[mid] - ref).max()),
+                                              "psnr_db": psnr(out_main[mid], ref)},
+                "fp32_vs_fp64": {"max_abs_err": float(np.abs(out32[mid] - ref).max()),
+                                 "psnr_db": psnr(out32[mid], ref)},
+                "view": "t=0.5"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,137 @@
+/*
+ * fvv.h — C ABI of the B300 VINet view-interpolation library (libfvv.so).
+ *
+ * The operation: given two adjacent camera frames I_left, I_right (H x W RGB)
+ * and a viewpoint position t in [0, 1], synthesise the virtual view between
+ * them with VINet (arXiv 2112.10603, Sec. 3.1): three VIBlocks estimate the
+ * bidirectional flow F_m->l, F_m->r and an occlusion mask M coarse to fine
+ * (Eq. 2, Table 3), the frames are backward-warped and blended
+ * (Eq. 1:  I_mid(u) = M(u) I_l(u + F_m->l(u)) + (1 - M(u)) I_r(u + F_m->r(u))),
+ * and a context-aware U-Net adds a residual (Sec. 3.1 "Refinement Network").
+ * The paper interpolates the midpoint and reaches other positions by stacking
+ * (Sec. 4.2); here t is also fed to every VIBlock as a constant input plane, so
+ * one call can serve any set of positions (t = 0.5 is the paper's midpoint).
+ *
+ * Conventions shared by every call:
+ *  - images are H x W x 3 float32, channels fastest (HWC), values in [0, 1];
+ *    several views are stored back to back (n x H x W x 3);
+ *  - sizes are padded internally to multiples of 16 with zeros on the bottom and
+ *    right, and the output is cropped back to H x W;
+ *  - all calls return 0 on success or a negative FVV_E* code; nothing throws
+ *    across the ABI; fvv_last_error() returns the calling thread's last message;
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  run calls are asynchronous on that stream and never synchronise
+ *    unless stated;
+ *  - an fvv_interp handle owns its device workspace, is used by one stream at a
+ *    time and is not thread-safe; the server (fvv_serve_*) is thread-safe.
+ */
+#ifndef FVV_H
+#define FVV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FVV_OK = 0,
+    FVV_EINVAL = -1,      /* bad argument (NULL pointer, t outside [0,1], bad enum) */
+    FVV_ESHAPE = -2,      /* H, W, n_views or weight count out of range */
+    FVV_ENOMEM = -3,      /* device or host allocation failed */
+    FVV_ECUDA = -4,       /* a CUDA call failed; the message names it */
+    FVV_EBUSY = -5,       /* admission refused: the HBM budget or queue is full */
+    FVV_ETIMEOUT = -6,    /* a bounded device wait gave up (kernel error flag) */
+    FVV_ESUPERSEDED = -7, /* request replaced by a newer one from the same user */
+    FVV_ENOTFOUND = -8    /* unknown ticket */
+};
+
+enum { FVV_FP32 = 0, FVV_BF16 = 1, FVV_FP8 = 2 };   /* convolution precision */
+enum { FVV_PAD_ZERO = 0, FVV_PAD_CIRCULAR = 1 };   /* border handling */
+enum { FVV_T_DIRECT = 0, FVV_T_RECURSIVE = 1 };    /* viewpoint handling */
+
+typedef struct {
+    int precision; /* FVV_FP32 (SIMT FP32 FMA), FVV_BF16 (tcgen05, FP32 accumulate), FVV_FP8 */
+    int pad_mode;  /* FVV_PAD_ZERO: zero conv padding, border-clamped sampling;
+                      FVV_PAD_CIRCULAR: everything wraps (needs H, W multiples of 16) */
+    int t_mode;    /* FVV_T_DIRECT: t plane = t;  FVV_T_RECURSIVE: dyadic stacking of
+                      midpoint views (t must be k / 2^n) */
+    int max_views; /* views per run call the workspace is sized for (>= 1) */
+    int max_cams;  /* cameras per batched call (>= 2) */
+} fvv_opts;
+
+typedef struct fvv_interp fvv_interp;
+
+/* Default options: FP32, zero padding, direct t, max_views 16, max_cams 2. */
+void fvv_default_opts(fvv_opts *opts);
+
+/* Create an interpolator for H x W frames.
+ * weights: host float32 blob, n_floats values, layers in Table 3 order (VIBlock 0,
+ *   1, 2, ContextNet, RefineNet), per layer W then b; conv W [Co][Ci][3][3],
+ *   convT W [Ci][Co][4][4].  Copied (and packed) at create; the caller keeps it.
+ * Returns FVV_ESHAPE if n_floats does not match the architecture or H, W are
+ * outside [16, 8192] (circular mode: not multiples of 16). */
+int fvv_interp_create(const float *weights, size_t n_floats, int H, int W,
+                      const fvv_opts *opts, fvv_interp **out);
+
+/* Synthesise n_views views between one camera pair.
+ * left, right: DEVICE pointers, H x W x 3 float32 each (caller-owned).
+ * t: HOST array of n_views positions in [0, 1] (0 = left camera, 1 = right).
+ * out: DEVICE pointer, n_views x H x W x 3 float32 (caller-owned).
+ * Asynchronous on `stream`.  n_views in [1, max_views]. */
+int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const float *t,
+                   int n_views, float *out, void *stream);
+
+/* Same as fvv_interp_run with HOST buffers: copies left/right to the device,
+ * runs, copies the views back into out (host), and synchronises `stream`.
+ * Page-locked host memory gives asynchronous copies; pageable memory works too. */
+int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t,
+                        int n_views, float *out, void *stream);
+
+/* Batched rig instant: n_cams frames, n_pairs camera pairs, uneven views per pair.
+ * cams: HOST array of n_cams DEVICE pointers (H x W x 3 float32 each).
+ * pair_left: HOST, n_pairs camera indices; pair p uses cams pair_left[p] and
+ *   pair_left[p] + 1.
+ * view_offsets: HOST, n_pairs + 1 prefix offsets; pair p owns views
+ *   [view_offsets[p], view_offsets[p+1]).
+ * t: HOST, view_offsets[n_pairs] positions.  out: DEVICE, total views x H x W x 3.
+ * All views of the call run as one batch (every layer one launch over all views);
+ * the total must not exceed max_views and n_cams must not exceed max_cams. */
+int fvv_interp_run_batch(fvv_interp *h, const float *const *cams, int n_cams,
+                         const int *pair_left, const int *view_offsets, const float *t,
+                         int n_pairs, float *out, void *stream);
+
+/* Bytes of device memory the handle holds (weights + workspace). */
+size_t fvv_interp_device_bytes(const fvv_interp *h);
+
+/* Number of kernel launches the last run call issued. */
+int fvv_interp_last_launches(const fvv_interp *h);
+
+/* Copy an intermediate of view `view` from the last run into `dst` (HOST,
+ * float32), synchronising the device first.  which: 0, 1, 2 = stage s flows and
+ * mask logit F^s, M^s (Eq. 2; Hp/2^(2-s) x Wp/2^(2-s) x 5, padded grid);
+ * 3 = I_blend (Eq. 1; Hp x Wp x 3); 4 = RefineNet output z before the sigmoid
+ * (Hp x Wp x 3).  n_floats must equal the size of that tensor (FVV_ESHAPE
+ * otherwise).  For tests and debugging; not needed on the product path. */
+int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_floats);
+
+/* Per-layer timing (the analogue of the paper's per-module latency, Table 2).
+ * fvv_interp_profile(h, 1) brackets every convolution launch of later runs with
+ * CUDA events on the run's stream (small overhead); 0 turns it off.  Both reset
+ * the counters.  fvv_interp_layer_stats synchronises those events and writes,
+ * per layer of Table 3 (n = 51 entries, blob order), the summed kernel time in ms,
+ * the summed algorithmic FLOPs (2 x MACs of the unpadded layer) and the number
+ * of launches since the last reset; any pointer may be NULL. */
+int fvv_interp_profile(fvv_interp *h, int enable);
+int fvv_interp_layer_stats(fvv_interp *h, double *ms, double *flops, int *launches, int n);
+
+void fvv_interp_destroy(fvv_interp *h);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *fvv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVV_H */

@@ -1,0 +1,190 @@
+"""ctypes binding of libfvv.so: the C ABI with the same names, arguments marshalled.
+
+Device buffers may be given as torch CUDA tensors (their data_ptr is passed) or
+as raw integer addresses; host buffers as numpy arrays.  Streams are torch
+streams, raw cudaStream_t integers, or None (torch's current stream).
+Every step of the computation runs in libfvv.so; there is no other path, and
+loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfvv.so")
+
+FVV_OK, FVV_EINVAL, FVV_ESHAPE, FVV_ENOMEM, FVV_ECUDA, FVV_EBUSY, FVV_ETIMEOUT, FVV_ESUPERSEDED, \
+    FVV_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FVV_FP32, FVV_BF16, FVV_FP8 = 0, 1, 2
+FVV_PAD_ZERO, FVV_PAD_CIRCULAR = 0, 1
+FVV_T_DIRECT, FVV_T_RECURSIVE = 0, 1
+
+ERROR_NAMES = {0: "FVV_OK", -1: "FVV_EINVAL", -2: "FVV_ESHAPE", -3: "FVV_ENOMEM", -4: "FVV_ECUDA",
+               -5: "FVV_EBUSY", -6: "FVV_ETIMEOUT", -7: "FVV_ESUPERSEDED", -8: "FVV_ENOTFOUND"}
+
+
+class FvvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fvv_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("pad_mode", ctypes.c_int), ("t_mode", ctypes.c_int),
+                ("max_views", ctypes.c_int), ("max_cams", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """The loaded libfvv.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfvv.so not built at {LIB_PATH}; run paper_2112_10603_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.fvv_last_error.restype = ctypes.c_char_p
+        L.fvv_default_opts.argtypes = [ctypes.POINTER(fvv_opts)]
+        L.fvv_interp_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(fvv_opts), ctypes.POINTER(_P)]
+        L.fvv_interp_run.argtypes = [_P, _P, _P, _P, ctypes.c_int, _P, _P]
+        L.fvv_interp_run_host.argtypes = [_P, _P, _P, _P, ctypes.c_int, _P, _P]
+        L.fvv_interp_run_batch.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P]
+        L.fvv_interp_device_bytes.argtypes = [_P]
+        L.fvv_interp_device_bytes.restype = ctypes.c_size_t
+        L.fvv_interp_last_launches.argtypes = [_P]
+        L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
+        L.fvv_interp_profile.argtypes = [_P, ctypes.c_int]
+        L.fvv_interp_layer_stats.argtypes = [_P, _P, _P, _P, ctypes.c_int]
+        L.fvv_interp_destroy.argtypes = [_P]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FVV_OK:
+        raise FvvError(rc, lib().fvv_last_error().decode())
+
+
+def _dev(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device address from {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _host_f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data
+
+
+def fvv_default_opts(**kw) -> fvv_opts:
+    o = fvv_opts()
+    lib().fvv_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def fvv_interp_create(weights, H: int, W: int, opts: fvv_opts | None = None) -> int:
+    w, wp = _host_f32(weights)
+    h = _P()
+    _check(lib().fvv_interp_create(wp, w.size, H, W, ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def fvv_interp_run(h: int, left, right, t, n_views: int, out, stream=None):
+    ta, tp = _host_f32(t)
+    _check(lib().fvv_interp_run(h, _dev(left), _dev(right), tp, n_views, _dev(out), _stream(stream)))
+
+
+def _host_buf(a, writable=False):
+    """(keepalive, address) of a host float32 buffer: numpy array or CPU torch tensor
+    (a pinned tensor keeps its page-locked address)."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float32":
+            raise ValueError("expected a contiguous float32 CPU tensor")
+        return a, a.data_ptr()
+    if writable:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+            raise ValueError("out must be a C-contiguous float32 numpy array")
+        return a, a.ctypes.data
+    return _host_f32(a)
+
+
+def fvv_interp_run_host(h: int, left, right, t, n_views: int, out, stream=None):
+    la, lp = _host_buf(left)
+    ra, rp = _host_buf(right)
+    ta, tp = _host_f32(t)
+    oa, op = _host_buf(out, writable=True)
+    _check(lib().fvv_interp_run_host(h, lp, rp, tp, n_views, op, _stream(stream)))
+
+
+def fvv_interp_run_batch(h: int, cams, pair_left, view_offsets, t, out, stream=None):
+    ptrs = (ctypes.c_void_p * len(cams))(*[_dev(c) for c in cams])
+    pl = np.ascontiguousarray(pair_left, dtype=np.int32)
+    vo = np.ascontiguousarray(view_offsets, dtype=np.int32)
+    ta, tp = _host_f32(t)
+    _check(lib().fvv_interp_run_batch(h, ptrs, len(cams), pl.ctypes.data, vo.ctypes.data, tp, len(pl),
+                                      _dev(out), _stream(stream)))
+
+
+def fvv_interp_device_bytes(h: int) -> int:
+    return lib().fvv_interp_device_bytes(h)
+
+
+def fvv_interp_last_launches(h: int) -> int:
+    return lib().fvv_interp_last_launches(h)
+
+
+def fvv_interp_peek(h: int, which: int, view: int, shape):
+    """Host copy (numpy float32, given shape) of an intermediate of the last run."""
+    out = np.empty(shape, np.float32)
+    _check(lib().fvv_interp_peek(h, which, view, out.ctypes.data, out.size))
+    return out
+
+
+def fvv_interp_profile(h: int, enable: bool):
+    _check(lib().fvv_interp_profile(h, int(enable)))
+
+
+N_LAYERS = 51
+
+
+def fvv_interp_layer_stats(h: int):
+    """(ms, flops, launches) arrays of length 51 since the last reset."""
+    ms = np.zeros(N_LAYERS)
+    fl = np.zeros(N_LAYERS)
+    ln = np.zeros(N_LAYERS, np.int32)
+    _check(lib().fvv_interp_layer_stats(h, ms.ctypes.data, fl.ctypes.data, ln.ctypes.data, N_LAYERS))
+    return ms, fl, ln
+
+
+def fvv_interp_destroy(h: int):
+    lib().fvv_interp_destroy(h)
+
+
+def fvv_last_error() -> str:
+    return lib().fvv_last_error().decode()

@@ -1,0 +1,184 @@
+// Plain FP32 convolution path: implicit GEMM on the CUDA cores (FFMA, no TF32).
+//
+// Conv2d 3x3 pad 1 (stride 1 or 2) and ConvTranspose2d 4x4 stride 2 pad 1, the
+// two operations of Table 3.  GEMM view: M = output pixels, N = C_out,
+// K = taps x C_in.  The transposed conv is split into its 4 output phases
+// (oy mod 2, ox mod 2); each phase is a 2x2-tap conv over the input grid:
+//   phase p = 0: taps ky in {1, 3} read input rows qy, qy - 1
+//   phase p = 1: taps ky in {0, 2} read input rows qy + 1, qy
+// (from oy = 2 iy - 1 + ky), and likewise for columns.
+//
+// Weights are packed on the host into [K][Co] rows (k = tap * Ci + ci), per
+// phase for the transposed conv.  Inputs/outputs may be channel slices of wider
+// tensors (pixel stride cs, channel offset coff), which is how concatenations
+// are formed without copies.
+#include "common.h"
+#include "kernels.h"
+
+namespace fvv {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ float load_in(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_in(const bf16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void store_out(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_out(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ int wrap_or_mark(int i, int n, int circ) {
+    if (circ) { i %= n; return i < 0 ? i + n : i; }
+    return (i < 0 || i >= n) ? -1 : i;
+}
+
+// Tap geometry of a transposed-conv phase: input offset of tap t (0/1) for phase p.
+__device__ __forceinline__ int convt_off(int p, int t) { return p == 0 ? -t : 1 - t; }
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(NT) conv_simt_kernel(ConvArgs a) {
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN];
+    const Tin *in = static_cast<const Tin *>(a.in);
+    Tout *out = static_cast<Tout *>(a.out);
+    const float *wp = static_cast<const float *>(a.w);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int phase = blockIdx.z;                 // 0 for conv, 0..3 for convT
+    const int py = phase >> 1, px = phase & 1;
+    const bool convt = a.kind == K_CONVT;
+    // GEMM rows: conv -> output pixels; convT -> input-grid pixels of this phase
+    const int GH = convt ? a.H : a.Ho, GW = convt ? a.W : a.Wo;
+    const int Mtot = a.N * GH * GW;
+    const int taps = convt ? 4 : 9;
+    const int K = taps * a.Ci;
+    if (convt) wp += (size_t)phase * K * a.Co;
+
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    // Per-thread A rows: element e = tid + i * NT -> (k = e % BK, m = e / BK)
+    int a_n[4], a_y[4], a_x[4];
+    bool a_ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int m = m0 + (tid + i * NT) / BK;
+        a_ok[i] = m < Mtot;
+        int mm = a_ok[i] ? m : 0;
+        a_x[i] = mm % GW;
+        int r = mm / GW;
+        a_y[i] = r % GH;
+        a_n[i] = r / GH;
+    }
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int e = tid + i * NT;
+            int kk = e % BK, m = e / BK;
+            int k = k0 + kk;
+            float v = 0.f;
+            if (a_ok[i] && k < K) {
+                int tap = k / a.Ci, ci = k - tap * a.Ci;
+                int iy, ix;
+                if (convt) {
+                    iy = a_y[i] + convt_off(py, tap >> 1);
+                    ix = a_x[i] + convt_off(px, tap & 1);
+                } else {
+                    int ky = tap / 3, kx = tap - ky * 3;
+                    iy = a_y[i] * a.stride + ky - 1;
+                    ix = a_x[i] * a.stride + kx - 1;
+                }
+                iy = wrap_or_mark(iy, a.H, a.circ);
+                ix = wrap_or_mark(ix, a.W, a.circ);
+                if (iy >= 0 && ix >= 0)
+                    v = load_in(in + ((size_t)(a_n[i] * a.H + iy) * a.W + ix) * a.in_cs + a.in_coff + ci);
+            }
+            As[kk][m] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int e = tid + i * NT;
+            int n = e % BN, kk = e / BN;
+            int k = k0 + kk, co = n0 + n;
+            Bs[kk][n] = (k < K && co < a.Co) ? __ldg(wp + (size_t)k * a.Co + co) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int m = m0 + ty * 4 + i;
+        if (m >= Mtot) continue;
+        int x = m % GW, r = m / GW, y = r % GH, n = r / GH;
+        int oy = convt ? 2 * y + py : y, ox = convt ? 2 * x + px : x;
+        Tout *dst = out + ((size_t)(n * a.Ho + oy) * a.Wo + ox) * a.out_cs + a.out_coff;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int co = n0 + tx * 4 + j;
+            if (co >= a.Co) continue;
+            float v = acc[i][j] + __ldg(a.bias + co);
+            if (a.relu) v = fmaxf(v, 0.f);
+            store_out(dst + co, v);
+        }
+    }
+}
+
+} // namespace
+
+int launch_conv_simt(const ConvArgs &a, bool in_bf16, bool out_bf16, cudaStream_t st) {
+    const bool convt = a.kind == K_CONVT;
+    const int GH = convt ? a.H : a.Ho, GW = convt ? a.W : a.Wo;
+    const long long M = (long long)a.N * GH * GW;
+    if (M <= 0) return FVV_OK;
+    if (M > (1ll << 31) / 2) { set_error("conv: too many pixels"); return FVV_ESHAPE; }
+    dim3 grid(ceil_div((int)M, BM), ceil_div(a.Co, BN), convt ? 4 : 1);
+    if (!in_bf16 && !out_bf16) conv_simt_kernel<float, float><<<grid, NT, 0, st>>>(a);
+    else if (in_bf16 && out_bf16) conv_simt_kernel<bf16, bf16><<<grid, NT, 0, st>>>(a);
+    else if (in_bf16) conv_simt_kernel<bf16, float><<<grid, NT, 0, st>>>(a);
+    else conv_simt_kernel<float, bf16><<<grid, NT, 0, st>>>(a);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+// Host packing of one layer for the SIMT kernel: [phase][K][Co] floats.
+void pack_simt(int kind, int Ci, int Co, const float *w, float *dst) {
+    if (kind == K_CONV) {
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < Ci; ++ci)
+                for (int co = 0; co < Co; ++co)
+                    dst[((size_t)tap * Ci + ci) * Co + co] = w[((size_t)co * Ci + ci) * 9 + tap];
+        return;
+    }
+    // convT: phase (py, px), tap (ty, tx) -> kernel index (ky, kx)
+    for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px)
+            for (int ty = 0; ty < 2; ++ty)
+                for (int tx = 0; tx < 2; ++tx) {
+                    int ky = py == 0 ? 1 + 2 * ty : 2 * ty, kx = px == 0 ? 1 + 2 * tx : 2 * tx;
+                    int phase = py * 2 + px, tap = ty * 2 + tx;
+                    for (int ci = 0; ci < Ci; ++ci)
+                        for (int co = 0; co < Co; ++co)
+                            dst[(((size_t)phase * 4 + tap) * Ci + ci) * Co + co] =
+                                w[((size_t)ci * Co + co) * 16 + ky * 4 + kx];
+                }
+}
+
+} // namespace fvv

@@ -1,0 +1,489 @@
+// VINet executor and C ABI (fvv_interp_*).
+//
+// Schedule of one batched forward (all views of the call are the batch N of
+// every per-view layer; per-camera work runs once per distinct camera):
+//   a0  pad + box pyramid of each camera frame
+//   a1  ContextNet on each camera (Table 3), keep the 4 stride-1 outputs
+//   a2  VIB0 on [I_l/4, I_r/4, t] -> F^0, logit M^0
+//   a3/a4  stages 1, 2: input assembly (upsample + warp), VIB_s, Eq. 2 residual
+//   a5  final warp + blend (Eq. 1) -> RefineNet input and I_blend
+//   a6  flow pyramid + context warps into the U-Net level tensors
+//   a7  RefineNet encoder/decoder (concatenations are channel slots of one tensor)
+//   a8  clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped
+#include <cstdarg>
+#include <cstring>
+#include <string>
+
+#include "interp.h"
+
+namespace fvv {
+
+static thread_local std::string g_err;
+thread_local int g_launches = 0;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+#define VIB_ROWS(i, cin)                                                                    \
+    {"vib" #i ".c0", K_CONV, cin, 128, 2, 1}, {"vib" #i ".c1", K_CONV, 128, 256, 2, 1},     \
+    {"vib" #i ".m0", K_CONV, 256, 256, 1, 1}, {"vib" #i ".m1", K_CONV, 256, 256, 1, 1},     \
+    {"vib" #i ".m2", K_CONV, 256, 256, 1, 1}, {"vib" #i ".m3", K_CONV, 256, 256, 1, 1},     \
+    {"vib" #i ".m4", K_CONV, 256, 256, 1, 1}, {"vib" #i ".m5", K_CONV, 256, 256, 1, 1},     \
+    {"vib" #i ".t0", K_CONVT, 256, 128, 2, 1}, {"vib" #i ".t1", K_CONVT, 128, 5, 2, 0}
+
+// Table 3, in weight-blob order.
+const LayerDef kLayers[kNumLayers] = {
+    VIB_ROWS(0, 7), VIB_ROWS(1, 18), VIB_ROWS(2, 18),
+    {"ctx.c0", K_CONV, 3, 16, 2, 1},   {"ctx.c1", K_CONV, 16, 16, 1, 1},
+    {"ctx.c2", K_CONV, 16, 32, 2, 1},  {"ctx.c3", K_CONV, 32, 32, 1, 1},
+    {"ctx.c4", K_CONV, 32, 64, 2, 1},  {"ctx.c5", K_CONV, 64, 64, 1, 1},
+    {"ctx.c6", K_CONV, 64, 128, 2, 1}, {"ctx.c7", K_CONV, 128, 128, 1, 1},
+    {"ref.e0a", K_CONV, 6, 32, 2, 1},    {"ref.e0b", K_CONV, 32, 32, 1, 1},
+    {"ref.e1a", K_CONV, 64, 64, 2, 1},   {"ref.e1b", K_CONV, 64, 64, 1, 1},
+    {"ref.e2a", K_CONV, 128, 128, 2, 1}, {"ref.e2b", K_CONV, 128, 128, 1, 1},
+    {"ref.e3a", K_CONV, 256, 256, 2, 1}, {"ref.e3b", K_CONV, 256, 256, 1, 1},
+    {"ref.d0", K_CONVT, 512, 128, 2, 1}, {"ref.d1", K_CONVT, 256, 64, 2, 1},
+    {"ref.d2", K_CONVT, 128, 32, 2, 1},  {"ref.d3", K_CONVT, 64, 16, 2, 1},
+    {"ref.out", K_CONV, 16, 3, 1, 0},
+};
+
+static size_t layer_wfloats(const LayerDef &L) { return (size_t)L.ci * L.co * (L.kind == K_CONV ? 9 : 16); }
+
+size_t blob_floats() {
+    size_t n = 0;
+    for (const auto &L : kLayers) n += layer_wfloats(L) + L.co;
+    return n;
+}
+
+int dalloc(fvv_interp *h, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return FVV_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        return FVV_ENOMEM;
+    }
+    h->allocs.push_back(*p);
+    h->dev_bytes += bytes;
+    return FVV_OK;
+}
+
+template <typename P> static int dalloc_t(fvv_interp *h, P **p, size_t bytes) {
+    void *q;
+    int rc = dalloc(h, &q, bytes);
+    *p = static_cast<P *>(q);
+    return rc;
+}
+
+static bool is_bf16(const fvv_interp *h) { return h->o.precision != FVV_FP32; }
+
+static cudaEvent_t pool_event(fvv_interp *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
+                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st);
+
+// One conv layer: FP32 SIMT on the FP32 path, tensor cores otherwise; bracketed
+// by events while profiling.
+static int conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
+                void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
+    if (!h->profiling) return conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+    const LayerDef &L = kLayers[li];
+    fvv_interp::ProfRec r;
+    r.layer = li;
+    r.flops = L.kind == K_CONV ? 2.0 * N * ((Hin - 1) / L.stride + 1) * ((Win - 1) / L.stride + 1) * L.co * 9.0 * L.ci
+                               : 2.0 * N * Hin * Win * 16.0 * L.ci * L.co;
+    r.a = pool_event(h);
+    r.b = pool_event(h);
+    FVV_CHECK_CUDA(cudaEventRecord(r.a, st));
+    int rc = conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+    FVV_CHECK_CUDA(cudaEventRecord(r.b, st));
+    h->prof.push_back(r);
+    return rc;
+}
+
+static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
+                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
+    const LayerDef &L = kLayers[li];
+    if (is_bf16(h)) return tc_conv(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+    ConvArgs a{};
+    a.in = in; a.in_cs = in_cs; a.in_coff = in_coff;
+    a.out = out; a.out_cs = out_cs; a.out_coff = out_coff;
+    a.w = h->w32 + h->w_off[li];
+    a.bias = h->bias + h->b_off[li];
+    a.N = N; a.H = Hin; a.W = Win; a.Ci = L.ci; a.Co = L.co;
+    a.kind = L.kind; a.stride = L.stride; a.relu = L.relu; a.circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
+    if (L.kind == K_CONV) { a.Ho = (Hin - 1) / L.stride + 1; a.Wo = (Win - 1) / L.stride + 1; }
+    else { a.Ho = 2 * Hin; a.Wo = 2 * Win; }
+    return launch_conv_simt(a, false, false, st);
+}
+
+template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
+    const int Hp = h->Hp, Wp = h->Wp, circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
+    const bool b16 = is_bf16(h);
+    const int cx0 = b16 ? 16 : 7, cx1 = b16 ? 32 : 18, cu0 = b16 ? 16 : 6;
+    ViewTab vt{h->d_cam_l, h->d_cam_r, h->d_t};
+    T *xb = (T *)h->xb, *ta = (T *)h->ta, *ma = (T *)h->ma, *mb = (T *)h->mb;
+    T *U[5];
+    for (int k = 0; k < 5; ++k) U[k] = (T *)h->u[k];
+
+    // a0: pyramid of every camera
+    FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2,
+                             b16 ? h->img0b : nullptr, st));
+    // a1: ContextNet, batched over cameras
+    {
+        int hh = Hp, ww = Wp;
+        const void *cur = b16 ? (const void *)h->img0b : (const void *)h->img0;
+        int cur_cs = b16 ? 16 : 3;
+        const int C[4] = {16, 32, 64, 128};
+        for (int k = 0; k < 4; ++k) {
+            FVV_TRY(conv(h, kCtx + 2 * k, cur, cur_cs, 0, n_cams, hh, ww, h->ctxt, C[k], 0, false, st));
+            hh /= 2; ww /= 2;
+            FVV_TRY(conv(h, kCtx + 2 * k + 1, h->ctxt, C[k], 0, n_cams, hh, ww, h->ctx[k], C[k], 0, false, st));
+            cur = h->ctx[k]; cur_cs = C[k];
+        }
+    }
+    // a2-a4: VIBlocks
+    for (int s = 0; s < 3; ++s) {
+        int hs = Hp >> (2 - s), ws = Wp >> (2 - s);
+        int cx = s == 0 ? cx0 : cx1;
+        if (s == 0) FVV_TRY(launch_vib0_input<T>(h->img2, vt, nv, hs, ws, xb, cx, st));
+        else FVV_TRY(launch_stage_input<T>(s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, xb, cx, st));
+        int base = s * 10;
+        FVV_TRY(conv(h, base + 0, xb, cx, 0, nv, hs, ws, ta, 128, 0, false, st));
+        FVV_TRY(conv(h, base + 1, ta, 128, 0, nv, hs / 2, ws / 2, ma, 256, 0, false, st));
+        T *src = ma, *dst = mb;
+        for (int k = 0; k < 6; ++k) {
+            FVV_TRY(conv(h, base + 2 + k, src, 256, 0, nv, hs / 4, ws / 4, dst, 256, 0, false, st));
+            T *tmp = src; src = dst; dst = tmp;
+        }
+        FVV_TRY(conv(h, base + 8, src, 256, 0, nv, hs / 4, ws / 4, ta, 128, 0, false, st));
+        FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st));
+        if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, hs, ws, circ, st));
+    }
+    // a5: final warp + blend
+    FVV_TRY(launch_final_blend<T>(h->img0, h->fm[2], vt, nv, Hp, Wp, circ, U[0], cu0, h->ib, st));
+    // a6 + a7: RefineNet with context warps.  Level tensors (channel slots):
+    //   U1 = [d2 | e0b | cL1 | cR1] (96), U2 = [d1 | e1b | cL2 | cR2] (192),
+    //   U3 = [d0 | e2b | cL3 | cR3] (384), U4 = [e3b | cL4 | cR4] (512)
+    const int ucs[5] = {cu0, 96, 192, 384, 512};
+    const int dec[5] = {0, 32, 64, 128, 0};    // decoder slot width at each level
+    const int encw[4] = {32, 64, 128, 256};    // encoder output width
+    const int ctxC[4] = {16, 32, 64, 128};
+    {
+        const void *cur = U[0];
+        int cur_cs = cu0, cur_off = 0;
+        int hh = Hp, ww = Wp;
+        for (int k = 0; k < 4; ++k) {
+            FVV_TRY(conv(h, kRef + 2 * k, cur, cur_cs, cur_off, nv, hh, ww, ma, encw[k], 0, false, st));
+            hh /= 2; ww /= 2;
+            int lvl = k + 1;
+            FVV_TRY(conv(h, kRef + 2 * k + 1, ma, encw[k], 0, nv, hh, ww, U[lvl], ucs[lvl], dec[lvl], false, st));
+            const float *fprev = k == 0 ? h->fm[2] : h->fk[k - 1];
+            int off_l = dec[lvl] + encw[k];
+            FVV_TRY(launch_ctx_warp<T>(fprev, k == 0 ? 5 : 4, h->fk[k], (const T *)h->ctx[k], ctxC[k], vt, nv, hh,
+                                       ww, circ, U[lvl], ucs[lvl], off_l, off_l + ctxC[k], st));
+            cur = U[lvl]; cur_cs = ucs[lvl]; cur_off = dec[lvl];
+        }
+        // decoders: d0 reads U4 (512) at 1/16 -> U3 slot 0; d_k reads U_{4-k}[0 : dec + enc] -> U_{3-k} slot 0
+        for (int k = 0; k < 4; ++k) {
+            int lvl = 4 - k;
+            void *dst = k < 3 ? (void *)U[lvl - 1] : (void *)ta;
+            int dst_cs = k < 3 ? ucs[lvl - 1] : 16;
+            FVV_TRY(conv(h, kRef + 8 + k, U[lvl], ucs[lvl], 0, nv, hh, ww, dst, dst_cs, 0, false, st));
+            hh *= 2; ww *= 2;
+        }
+        FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st));
+    }
+    return FVV_OK;
+}
+
+int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
+    g_launches = 0;
+    int rc = is_bf16(h) ? forward_t<bf16>(h, n_cams, nv, st) : forward_t<float>(h, n_cams, nv, st);
+    h->last_launches = g_launches;
+    return rc;
+}
+
+// Pack weights and allocate the workspace.
+static int create_impl(fvv_interp *h, const float *blob) {
+    const int Hp = h->Hp, Wp = h->Wp, V = h->o.max_views, C = h->o.max_cams;
+    const size_t P = (size_t)Hp * Wp;
+    const bool b16 = is_bf16(h);
+    const size_t es = b16 ? 2 : 4; // conv activation element size
+    // FP32 weights (SIMT path) and biases
+    size_t wtot = 0, btot = 0;
+    for (int i = 0; i < kNumLayers; ++i) {
+        h->w_off[i] = wtot; h->b_off[i] = btot;
+        wtot += layer_wfloats(kLayers[i]); btot += kLayers[i].co;
+    }
+    {
+        std::vector<float> packed(wtot), bias(btot);
+        size_t off = 0;
+        for (int i = 0; i < kNumLayers; ++i) {
+            const LayerDef &L = kLayers[i];
+            pack_simt(L.kind, L.ci, L.co, blob + off, packed.data() + h->w_off[i]);
+            off += layer_wfloats(L);
+            memcpy(bias.data() + h->b_off[i], blob + off, sizeof(float) * L.co);
+            off += L.co;
+        }
+        FVV_TRY(dalloc_t(h, &h->bias, btot * 4));
+        FVV_CHECK_CUDA(cudaMemcpy(h->bias, bias.data(), btot * 4, cudaMemcpyHostToDevice));
+        if (!b16) {
+            FVV_TRY(dalloc_t(h, &h->w32, wtot * 4));
+            FVV_CHECK_CUDA(cudaMemcpy(h->w32, packed.data(), wtot * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    if (b16) FVV_TRY(tc_prepare(h, blob));
+    // per-camera
+    FVV_TRY(dalloc_t(h, &h->img0, C * P * 3 * 4));
+    FVV_TRY(dalloc_t(h, &h->img1, C * P / 4 * 3 * 4));
+    FVV_TRY(dalloc_t(h, &h->img2, C * P / 16 * 3 * 4));
+    if (b16) FVV_TRY(dalloc_t(h, &h->img0b, C * P * 16 * 2));
+    const int ctxC[4] = {16, 32, 64, 128};
+    for (int k = 0; k < 4; ++k) FVV_TRY(dalloc(h, &h->ctx[k], C * (P >> (2 * k + 2)) * ctxC[k] * es));
+    FVV_TRY(dalloc(h, &h->ctxt, C * (P / 4) * 16 * es));
+    // per-view
+    FVV_TRY(dalloc(h, &h->xb, V * P * (b16 ? 32 : 18) * es));
+    FVV_TRY(dalloc(h, &h->ta, V * P * 32 * es));
+    FVV_TRY(dalloc(h, &h->ma, V * P * 16 * es));
+    FVV_TRY(dalloc(h, &h->mb, V * P * 16 * es));
+    for (int s = 0; s < 3; ++s) FVV_TRY(dalloc_t(h, &h->fm[s], V * (P >> (2 * (2 - s))) * 5 * 4));
+    FVV_TRY(dalloc_t(h, &h->ib, V * P * 3 * 4));
+    for (int k = 0; k < 4; ++k) FVV_TRY(dalloc_t(h, &h->fk[k], V * (P >> (2 * k + 2)) * 4 * 4));
+    FVV_TRY(dalloc_t(h, &h->z, V * P * 3 * 4));
+    const int ucs[5] = {b16 ? 16 : 6, 96, 192, 384, 512};
+    for (int k = 0; k < 5; ++k) FVV_TRY(dalloc(h, &h->u[k], V * (P >> (2 * k)) * ucs[k] * es));
+    // the U-Net level tensors must start as zeros only where nothing writes: every
+    // slot is written each run, so no clearing is needed.
+    FVV_TRY(dalloc_t(h, &h->d_cam_l, V * 4));
+    FVV_TRY(dalloc_t(h, &h->d_cam_r, V * 4));
+    FVV_TRY(dalloc_t(h, &h->d_t, V * 4));
+    FVV_TRY(dalloc_t(h, &h->d_cams, C * sizeof(float *)));
+    FVV_TRY(dalloc_t(h, &h->d_err, 64));
+    FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, 64));
+    FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + C * sizeof(float *) + 64));
+    FVV_CHECK_CUDA(cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming));
+    return FVV_OK;
+}
+
+// Upload the view table and camera pointers through pinned staging.
+static int upload_tables(fvv_interp *h, const float *const *cams, int n_cams, const int *cam_l, const int *cam_r,
+                         const float *t, int nv, cudaStream_t st) {
+    FVV_CHECK_CUDA(cudaEventSynchronize(h->stage_done)); // previous upload finished reading the staging
+    const int V = h->o.max_views;
+    char *s = h->h_stage;
+    memcpy(s, cam_l, nv * 4);
+    memcpy(s + V * 4, cam_r, nv * 4);
+    memcpy(s + V * 8, t, nv * 4);
+    memcpy(s + V * 12, cams, n_cams * sizeof(float *));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_l, s, nv * 4, cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_r, s + V * 4, nv * 4, cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_t, s + V * 8, nv * 4, cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cams, s + V * 12, n_cams * sizeof(float *), cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaEventRecord(h->stage_done, st));
+    return FVV_OK;
+}
+
+static int check_t(const float *t, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!(t[i] >= 0.f && t[i] <= 1.f)) { set_error("t[%d] = %g outside [0, 1]", i, t[i]); return FVV_EINVAL; }
+    return FVV_OK;
+}
+
+} // namespace fvv
+
+using namespace fvv;
+
+extern "C" {
+
+void fvv_default_opts(fvv_opts *o) {
+    if (!o) return;
+    o->precision = FVV_FP32;
+    o->pad_mode = FVV_PAD_ZERO;
+    o->t_mode = FVV_T_DIRECT;
+    o->max_views = 16;
+    o->max_cams = 2;
+}
+
+const char *fvv_last_error(void) { return g_err.c_str(); }
+
+int fvv_interp_create(const float *weights, size_t n_floats, int H, int W, const fvv_opts *opts,
+                      fvv_interp **out) {
+    clear_error();
+    if (!weights || !out) { set_error("NULL argument"); return FVV_EINVAL; }
+    *out = nullptr;
+    fvv_opts o;
+    fvv_default_opts(&o);
+    if (opts) o = *opts;
+    if (n_floats != blob_floats()) {
+        set_error("weight blob has %zu floats, the architecture needs %zu", n_floats, blob_floats());
+        return FVV_ESHAPE;
+    }
+    if (o.precision < FVV_FP32 || o.precision > FVV_FP8 || (o.pad_mode != FVV_PAD_ZERO && o.pad_mode != FVV_PAD_CIRCULAR) ||
+        (o.t_mode != FVV_T_DIRECT && o.t_mode != FVV_T_RECURSIVE)) {
+        set_error("bad option value"); return FVV_EINVAL;
+    }
+    if (H < 16 || W < 16 || H > 8192 || W > 8192) { set_error("H, W = %d, %d outside [16, 8192]", H, W); return FVV_ESHAPE; }
+    if (o.pad_mode == FVV_PAD_CIRCULAR && (H % 16 || W % 16)) {
+        set_error("circular padding needs H, W multiples of 16"); return FVV_ESHAPE;
+    }
+    if (o.max_views < 1 || o.max_views > 1024 || o.max_cams < 2 || o.max_cams > 64) {
+        set_error("max_views in [1, 1024] and max_cams in [2, 64] required"); return FVV_ESHAPE;
+    }
+    fvv_interp *h = new fvv_interp();
+    h->H = H; h->W = W; h->o = o;
+    h->Hp = (H + 15) / 16 * 16; h->Wp = (W + 15) / 16 * 16;
+    int rc = create_impl(h, weights);
+    if (rc != FVV_OK) { fvv_interp_destroy(h); return rc; }
+    *out = h;
+    return FVV_OK;
+}
+
+int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const float *t, int n_views, float *out,
+                   void *stream) {
+    clear_error();
+    if (!h || !left || !right || !t || !out) { set_error("NULL argument"); return FVV_EINVAL; }
+    if (n_views < 1 || n_views > h->o.max_views) {
+        set_error("n_views = %d outside [1, %d]", n_views, h->o.max_views); return FVV_ESHAPE;
+    }
+    FVV_TRY(check_t(t, n_views));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> cl(n_views, 0), cr(n_views, 1);
+    const float *cams[2] = {left, right};
+    FVV_TRY(upload_tables(h, cams, 2, cl.data(), cr.data(), t, n_views, st));
+    FVV_TRY(interp_forward(h, 2, n_views, st));
+    int launches = h->last_launches;
+    int rc = launch_output(h->ib, h->z, 3, n_views, h->Hp, h->Wp, h->H, h->W, out, st);
+    h->last_launches = launches + 1;
+    return rc;
+}
+
+int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
+                        float *out, void *stream) {
+    clear_error();
+    if (!h || !left || !right || !t || !out) { set_error("NULL argument"); return FVV_EINVAL; }
+    if (n_views < 1 || n_views > h->o.max_views) {
+        set_error("n_views = %d outside [1, %d]", n_views, h->o.max_views); return FVV_ESHAPE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t img = (size_t)h->H * h->W * 3;
+    if (!h->d_in) {
+        FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
+        FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
+    }
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_in, left, img * 4, cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_in + img, right, img * 4, cudaMemcpyHostToDevice, st));
+    FVV_TRY(fvv_interp_run(h, h->d_in, h->d_in + img, t, n_views, h->d_out, stream));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(out, h->d_out, n_views * img * 4, cudaMemcpyDeviceToHost, st));
+    FVV_CHECK_CUDA(cudaStreamSynchronize(st));
+    return FVV_OK;
+}
+
+int fvv_interp_run_batch(fvv_interp *h, const float *const *cams, int n_cams, const int *pair_left,
+                         const int *view_offsets, const float *t, int n_pairs, float *out, void *stream) {
+    clear_error();
+    if (!h || !cams || !pair_left || !view_offsets || !t || !out) { set_error("NULL argument"); return FVV_EINVAL; }
+    if (n_cams < 2 || n_cams > h->o.max_cams || n_pairs < 1) { set_error("n_cams/n_pairs out of range"); return FVV_ESHAPE; }
+    if (view_offsets[0] != 0) { set_error("view_offsets[0] must be 0"); return FVV_EINVAL; }
+    int nv = view_offsets[n_pairs];
+    if (nv < 1 || nv > h->o.max_views) { set_error("total views %d outside [1, %d]", nv, h->o.max_views); return FVV_ESHAPE; }
+    FVV_TRY(check_t(t, nv));
+    std::vector<int> cl(nv), cr(nv);
+    for (int p = 0; p < n_pairs; ++p) {
+        if (pair_left[p] < 0 || pair_left[p] + 1 >= n_cams) { set_error("pair_left[%d] out of range", p); return FVV_EINVAL; }
+        if (view_offsets[p + 1] < view_offsets[p]) { set_error("view_offsets not monotone"); return FVV_EINVAL; }
+        for (int v = view_offsets[p]; v < view_offsets[p + 1]; ++v) { cl[v] = pair_left[p]; cr[v] = pair_left[p] + 1; }
+    }
+    for (int c = 0; c < n_cams; ++c)
+        if (!cams[c]) { set_error("cams[%d] is NULL", c); return FVV_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    FVV_TRY(upload_tables(h, cams, n_cams, cl.data(), cr.data(), t, nv, st));
+    FVV_TRY(interp_forward(h, n_cams, nv, st));
+    int launches = h->last_launches;
+    int rc = launch_output(h->ib, h->z, 3, nv, h->Hp, h->Wp, h->H, h->W, out, st);
+    h->last_launches = launches + 1;
+    return rc;
+}
+
+int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_floats) {
+    clear_error();
+    if (!h || !dst || which < 0 || which > 4 || view < 0 || view >= h->o.max_views) {
+        set_error("bad peek arguments"); return FVV_EINVAL;
+    }
+    size_t P = (size_t)h->Hp * h->Wp;
+    const float *src;
+    size_t n;
+    if (which < 3) { n = (P >> (2 * (2 - which))) * 5; src = h->fm[which]; }
+    else { n = P * 3; src = which == 3 ? h->ib : h->z; }
+    if (n_floats != n) { set_error("peek: tensor has %zu floats, got %zu", n, n_floats); return FVV_ESHAPE; }
+    FVV_CHECK_CUDA(cudaDeviceSynchronize());
+    FVV_CHECK_CUDA(cudaMemcpy(dst, src + (size_t)view * n, n * 4, cudaMemcpyDeviceToHost));
+    return FVV_OK;
+}
+
+static void prof_reset(fvv_interp *h) {
+    for (auto &r : h->prof) { h->ev_pool.push_back(r.a); h->ev_pool.push_back(r.b); }
+    h->prof.clear();
+}
+
+int fvv_interp_profile(fvv_interp *h, int enable) {
+    clear_error();
+    if (!h) { set_error("NULL handle"); return FVV_EINVAL; }
+    FVV_CHECK_CUDA(cudaDeviceSynchronize());
+    prof_reset(h);
+    h->profiling = enable != 0;
+    return FVV_OK;
+}
+
+int fvv_interp_layer_stats(fvv_interp *h, double *ms, double *flops, int *launches, int n) {
+    clear_error();
+    if (!h || n < kNumLayers) { set_error("need a handle and n >= %d", kNumLayers); return FVV_EINVAL; }
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = 0;
+        if (flops) flops[i] = 0;
+        if (launches) launches[i] = 0;
+    }
+    for (auto &r : h->prof) {
+        FVV_CHECK_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        FVV_CHECK_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        if (ms) ms[r.layer] += t;
+        if (flops) flops[r.layer] += r.flops;
+        if (launches) launches[r.layer] += 1;
+    }
+    prof_reset(h);
+    return FVV_OK;
+}
+
+size_t fvv_interp_device_bytes(const fvv_interp *h) { return h ? h->dev_bytes : 0; }
+int fvv_interp_last_launches(const fvv_interp *h) { return h ? h->last_launches : 0; }
+
+void fvv_interp_destroy(fvv_interp *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->stage_done) cudaEventDestroy(h->stage_done);
+    prof_reset(h);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+} // extern "C"

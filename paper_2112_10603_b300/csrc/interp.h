@@ -1,0 +1,72 @@
+// Network executor: layer table, packed weights, workspace and the layer schedule.
+#pragma once
+#include <vector>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace fvv {
+
+struct LayerDef {
+    const char *name;
+    int kind, ci, co, stride, relu;
+};
+
+constexpr int kNumLayers = 51;
+extern const LayerDef kLayers[kNumLayers];
+// first layer index of each sub-network
+constexpr int kVib0 = 0, kVib1 = 10, kVib2 = 20, kCtx = 30, kRef = 38;
+
+size_t blob_floats();
+
+// Packed weights of one layer for the tensor-core kernels.
+struct TcWeights {
+    void *w = nullptr;      // device, [phase*taps][Co_pad][Ci_pad] bf16 (or fp8) K-major
+    float *scale = nullptr; // FP8: per-output-channel dequantisation scale
+    int ci_pad = 0, co_pad = 0;
+};
+
+} // namespace fvv
+
+struct fvv_interp {
+    int H = 0, W = 0, Hp = 0, Wp = 0;
+    fvv_opts o{};
+    // weights
+    float *w32 = nullptr;    // SIMT-packed FP32 weights, all layers
+    float *bias = nullptr;   // all biases
+    size_t w_off[fvv::kNumLayers] = {}, b_off[fvv::kNumLayers] = {};
+    fvv::TcWeights tc[fvv::kNumLayers];
+    // per-camera buffers
+    float *img0 = nullptr, *img1 = nullptr, *img2 = nullptr;
+    fvv::bf16 *img0b = nullptr;
+    void *ctx[4] = {}, *ctxt = nullptr;
+    // per-view buffers
+    void *xb = nullptr, *ta = nullptr, *ma = nullptr, *mb = nullptr;
+    float *fm[3] = {}, *ib = nullptr, *fk[4] = {}, *z = nullptr;
+    void *u[5] = {};
+    // view table and camera pointer table (device) + pinned host staging
+    int *d_cam_l = nullptr, *d_cam_r = nullptr;
+    float *d_t = nullptr;
+    const float **d_cams = nullptr;
+    char *h_stage = nullptr;
+    cudaEvent_t stage_done = nullptr;
+    // staging for host-buffer calls
+    float *d_in = nullptr, *d_out = nullptr;
+    int *d_err = nullptr; // device error word written by bounded waits
+    size_t dev_bytes = 0;
+    int last_launches = 0;
+    std::vector<void *> allocs;
+    // per-layer event timing (fvv_interp_profile)
+    struct ProfRec { int layer; double flops; cudaEvent_t a, b; };
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace fvv {
+int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st);
+int dalloc(fvv_interp *h, void **p, size_t bytes);
+int tc_prepare(fvv_interp *h, const float *blob);
+int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
+            void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st);
+} // namespace fvv

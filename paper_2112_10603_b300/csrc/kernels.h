@@ -1,0 +1,35 @@
+// Kernel launchers (one per kernel family); all return FVV_OK or an FVV_E* code.
+#pragma once
+#include "common.h"
+
+namespace fvv {
+
+// Per-view lookup table in device memory: cameras of the view's pair and its t.
+struct ViewTab {
+    const int *cam_l;
+    const int *cam_r;
+    const float *t;
+};
+
+// FP32 SIMT implicit-GEMM conv / convT (weights packed by pack_simt).
+int launch_conv_simt(const ConvArgs &a, bool in_bf16, bool out_bf16, cudaStream_t st);
+void pack_simt(int kind, int Ci, int Co, const float *w, float *dst);
+
+int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float *img0,
+                     float *img1, float *img2, bf16 *img0_b16, cudaStream_t st);
+template <typename T>
+int launch_vib0_input(const float *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st);
+template <typename T>
+int launch_stage_input(const float *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w, int circ,
+                       T *x, int cs, cudaStream_t st);
+int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ, cudaStream_t st);
+template <typename T>
+int launch_final_blend(const float *img0, const float *FM, const ViewTab &vt, int nv, int h, int w, int circ,
+                       T *u0, int cs, float *ib, cudaStream_t st);
+template <typename T>
+int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, const ViewTab &vt, int nv,
+                    int h, int w, int circ, T *dst, int dst_cs, int off_l, int off_r, cudaStream_t st);
+int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *out,
+                  cudaStream_t st);
+
+} // namespace fvv

@@ -1,0 +1,61 @@
+"""The C-ABI library loads, exports every symbol its headers declare, and rejects
+bad arguments before touching a GPU (CPU only)."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2112_10603_b300 as fvv
+from paper_2112_10603_b300 import build as fvv_build
+from synth import weights
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fvv_build.build()
+    return fvv.lib()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(fvv_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_blob_size_matches_generator(lib):
+    with pytest.raises(fvv.FvvError) as e:
+        fvv.fvv_interp_create(np.zeros(weights.n_floats() - 1, np.float32), 64, 64)
+    assert e.value.code == fvv.FVV_ESHAPE
+    assert str(weights.n_floats()) in str(e.value)
+
+
+@pytest.mark.parametrize("H,W,opts,code", [
+    (8, 64, {}, fvv.FVV_ESHAPE),
+    (64, 9000, {}, fvv.FVV_ESHAPE),
+    (72, 64, {"pad_mode": fvv.FVV_PAD_CIRCULAR}, fvv.FVV_ESHAPE),
+    (64, 64, {"precision": 7}, fvv.FVV_EINVAL),
+    (64, 64, {"max_views": 0}, fvv.FVV_ESHAPE),
+])
+def test_create_rejects_bad_arguments(lib, H, W, opts, code):
+    blob = np.zeros(weights.n_floats(), np.float32)
+    with pytest.raises(fvv.FvvError) as e:
+        fvv.fvv_interp_create(blob, H, W, fvv.fvv_default_opts(**opts))
+    assert e.value.code == code
+
+
+def test_default_opts(lib):
+    o = fvv.fvv_default_opts()
+    assert (o.precision, o.pad_mode, o.t_mode, o.max_views, o.max_cams) == (0, 0, 0, 16, 2)
