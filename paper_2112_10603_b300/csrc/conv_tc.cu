@@ -1,13 +1,485 @@
-// Tensor-core convolution path (placeholder until the tcgen05 kernel lands).
+// Tensor-core convolutions: tcgen05 BF16 implicit GEMM, FP32 accumulation in TMEM.
+//
+// GEMM view of a Table-3 layer: M = output pixels (128 per tile, a TH x TW
+// rectangle of one image), N = C_out (one tile, <= 256), K = taps x C_in.
+// K is walked in blocks of one tap x CK channels; for every block TMA copies
+//   A: the input patch of the tile shifted by the tap (tiled 4-D map over
+//      [N][H][W][C]; out-of-range rows/columns arrive as zeros = conv padding),
+//   B: the tap's [C_out][CK] weight slice,
+// into 128B/64B/32B-swizzled shared memory, and one thread issues CK/16
+// tcgen05.mma (M=128, N=C_out, K=16).
+//   * stride-2 conv: the input is viewed as pixel pairs [N][H/2][2][W/2][2C]
+//     (5-D map), so tap (ky, kx) is a plain box at (pair column ox-1 or ox,
+//     half = kx!=1, row pair oy-1 or oy, row parity = ky!=1);
+//   * 4x4 stride-2 transposed conv: 4 output phases, each a 2x2-tap conv on the
+//     input grid (phase p: taps read rows q - t (p=0) or q + 1 - t (p=1)).
+// Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer (+ TMEM owner),
+// warps 2-5 = epilogue (TMEM -> registers -> bias, ReLU, BF16/FP32 -> global).
+// The accumulator is double-buffered in TMEM so the epilogue of one tile runs
+// under the main loop of the next; CTAs loop over tiles (persistent grid).
+// Every mbarrier wait is bounded: on expiry the kernel records an error code in
+// global memory, tells the other roles to stop, drains and frees TMEM, returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <vector>
+
 #include "interp.h"
+#include "tc_ptx.h"
 
 namespace fvv {
-int tc_prepare(fvv_interp *, const float *) {
-    set_error("tensor-core path not built");
+
+namespace {
+
+enum { MODE_S1 = 0, MODE_S2 = 1, MODE_T = 2 };
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000ll; // ~2 s: far beyond any legitimate wait
+
+struct TcParams {
+    int mode;
+    int n_img, gh, gw;      // GEMM grid (conv: output size; convT: input size)
+    int th_log, tw_log;     // tile = (1 << th_log) x (1 << tw_log) = 128 pixels
+    int tiles_y, tiles_x, num_tiles;
+    int nck;                // channel blocks per tap
+    int taps;               // 9 (conv) or 4 (convT phase)
+    int in_cs, in_coff;     // input pixel stride / channel offset (elements)
+    int co;                 // real output channels
+    int relu, out_f32;
+    void *out;
+    int out_cs, out_coff, out_h, out_w;
+    const float *bias;
+    int *err;
+};
+
+struct __align__(8) Bars {
+    uint64_t full[8], empty[8], tmem_full[2], tmem_empty[2], drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort, int *err, int code) {
+    long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255) {
+            if (*abort) return false;
+            long long now = clock64();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitCycles) {
+                *abort = 1;
+                atomicExch(err, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase, int &n, int &y0, int &x0) {
+    int per_phase = p.n_img * p.tiles_y * p.tiles_x;
+    phase = t / per_phase;
+    int r = t - phase * per_phase;
+    int tx = r % p.tiles_x;
+    r /= p.tiles_x;
+    int ty = r % p.tiles_y;
+    n = r / p.tiles_y;
+    y0 = ty << p.th_log;
+    x0 = tx << p.tw_log;
+}
+
+template <int BN, int CK, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+    constexpr uint32_t A_BYTES = 128 * CK * 2, B_BYTES = BN * CK * 2;
+    constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
+    constexpr uint32_t TMEM_COLS = (2 * BN) <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+    constexpr uint32_t IDESC = ptx::make_idesc(128, BN, 1, 1);
+    constexpr int ROW_BYTES = CK * 2;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_STRIDE;
+    Bars *bars = (Bars *)(sB + STAGES * B_STRIDE);
+    volatile int *abort = &bars->abort;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(ptx::smem_u32(&bars->tmem_full[a]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->tmem_empty[a]), 128);
+        }
+        ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
+        bars->abort = 0;
+        ptx::fence_barrier_init();
+        ptx::fence_proxy_async_smem();
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    const int kblocks = p.taps * p.nck;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase_bit = 0;
+            long long issued = 0;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+                int ph, n, y0, x0;
+                tile_coords(p, t, ph, n, y0, x0);
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    if (!wait_bar(ptx::smem_u32(&bars->empty[stage]), phase_bit ^ 1, abort, p.err, 1)) break;
+                    int tap = kb / p.nck, c0 = (kb - tap * p.nck) * CK;
+                    uint32_t fb = ptx::smem_u32(&bars->full[stage]);
+                    ptx::mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES);
+                    uint32_t da = ptx::smem_u32(sA + stage * A_STRIDE), db = ptx::smem_u32(sB + stage * B_STRIDE);
+                    if (p.mode == MODE_S1) {
+                        int ky = tap / 3, kx = tap - 3 * (tap / 3);
+                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1, y0 + ky - 1, n);
+                        ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
+                    } else if (p.mode == MODE_S2) {
+                        int ky = tap / 3, kx = tap - 3 * (tap / 3);
+                        int half = kx == 1 ? 0 : 1, rpar = ky == 1 ? 0 : 1;
+                        ptx::tma_load_5d(da, &tmA, fb, half * p.in_cs + p.in_coff + c0, x0 - (kx == 0 ? 1 : 0), rpar,
+                                         y0 - (ky == 0 ? 1 : 0), n);
+                        ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
+                    } else {
+                        int py = ph >> 1, px = ph & 1, ty = tap >> 1, tx = tap & 1;
+                        int dy = py == 0 ? -ty : 1 - ty, dx = px == 0 ? -tx : 1 - tx;
+                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + dx, y0 + dy, n);
+                        ptx::tma_load_3d(db, &tmB, fb, c0, 0, ph * 4 + tap);
+                    }
+                    ++issued;
+                    if (++stage == STAGES) { stage = 0; phase_bit ^= 1; }
+                }
+            }
+            if (*abort) {
+                // let every copy still in flight land before the CTA exits
+                for (int s = 0; s < STAGES && issued > 0; ++s) {
+                    long long k = issued - 1 - s;
+                    if (k < 0) break;
+                    int st = (int)(k % STAGES);
+                    uint32_t par = (uint32_t)((k / STAGES) & 1);
+                    long long t0 = clock64();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full[st]), par) && clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase_bit = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
+                ptx::tc_fence_after();
+                uint32_t d = tmem + acc * BN;
+                bool ok = true;
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    if (!wait_bar(ptx::smem_u32(&bars->full[stage]), phase_bit, abort, p.err, 3)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    uint32_t a0 = ptx::smem_u32(sA + stage * A_STRIDE), b0 = ptx::smem_u32(sB + stage * B_STRIDE);
+#pragma unroll
+                    for (int k = 0; k < CK / 16; ++k) {
+                        uint64_t ad = ptx::smem_desc(a0 + k * 32, ROW_BYTES);
+                        uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
+                        ptx::mma_bf16(d, ad, bd, IDESC, (kb | k) != 0);
+                    }
+                    issued_any = true;
+                    ptx::mma_commit(ptx::smem_u32(&bars->empty[stage]));
+                    if (++stage == STAGES) { stage = 0; phase_bit ^= 1; }
+                }
+                if (!ok) break;
+                ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+            if (*abort && issued_any) {
+                // wait (bounded) for the MMAs already issued before TMEM is freed
+                ptx::mma_commit(ptx::smem_u32(&bars->drain));
+                long long t0 = clock64();
+                while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->drain), 0) && clock64() - t0 < kWaitCycles) {}
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;           // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;    // tile row = accumulator lane
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        const int tw = 1 << p.tw_log;
+        const int dy = row >> p.tw_log, dx = row & (tw - 1);
+        for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            int ph, n, y0, x0;
+            tile_coords(p, t, ph, n, y0, x0);
+            if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
+            ptx::tc_fence_after();
+            int gy = y0 + dy, gx = x0 + dx;
+            bool valid = gy < p.gh && gx < p.gw;
+            int oy = gy, ox = gx;
+            if (p.mode == MODE_T) { oy = 2 * gy + (ph >> 1); ox = 2 * gx + (ph & 1); }
+            size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
+            uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                uint32_t r[16];
+                __syncwarp();
+                ptx::tmem_ld16(tbase + c, r);
+                ptx::tmem_ld_wait();
+                if (valid) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    int co = c + j;
+                    float x = __uint_as_float(r[j]) + (co < p.co ? __ldg(p.bias + co) : 0.f);
+                    v[j] = p.relu ? fmaxf(x, 0.f) : x;
+                }
+                if (p.out_f32) {
+                    float *dst = (float *)p.out + pix * p.out_cs + p.out_coff + c;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c + j < p.co) dst[j] = v[j];
+                } else {
+                    bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + c;
+                    if (c + 16 <= p.co) {
+                        uint4 w0, w1;
+                        __nv_bfloat162 h[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        memcpy(&w0, &h[0], 16);
+                        memcpy(&w1, &h[4], 16);
+                        reinterpret_cast<uint4 *>(dst)[0] = w0;
+                        reinterpret_cast<uint4 *>(dst)[1] = w1;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c + j < p.co) dst[j] = __float2bfloat16_rn(v[j]);
+                    }
+                }
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(ptx::smem_u32(&bars->tmem_empty[acc]));
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps, weight packing, tile shape choice, launch.
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encoder() {
+    if (g_encode) return FVV_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        set_error("cuTensorMapEncodeTiled unavailable (%s)", cudaGetErrorString(e));
+        return FVV_ECUDA;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return FVV_OK;
+}
+
+CUtensorMapSwizzle swz_for(int ck_bytes) {
+    return ck_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                           : (ck_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+int encode(CUtensorMap *m, int rank, void *base, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
+           const cuuint32_t *box, int ck_bytes) {
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, base, dims, strides_bytes, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz_for(ck_bytes), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d), rank %d", (int)r, rank);
+        return FVV_ECUDA;
+    }
+    return FVV_OK;
+}
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+int ci_pad_of(int ci) { return ci <= 16 ? 16 : (ci <= 32 ? 32 : (ci + 63) / 64 * 64); }
+int ck_of(int ci_pad) { return ci_pad >= 64 ? 64 : ci_pad; }
+
+struct Shape { int th_log, tw_log; };
+
+// Tile rectangle with the fewest tiles covering gh x gw (ties: wider).
+Shape pick_shape(int gh, int gw) {
+    Shape best{3, 4};
+    long best_tiles = -1;
+    for (int tw_log = 7; tw_log >= 3; --tw_log) {
+        int th_log = 7 - tw_log;
+        long tiles = (long)ceil_div(gh, 1 << th_log) * ceil_div(gw, 1 << tw_log);
+        if (best_tiles < 0 || tiles < best_tiles) { best_tiles = tiles; best = {th_log, tw_log}; }
+    }
+    return best;
+}
+
+template <int BN, int CK> struct Cfg {
+    static constexpr uint32_t A = ((128 * CK * 2) + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
+    static constexpr int STAGES = (200 * 1024) / (A + B) > 8 ? 8 : (200 * 1024) / (A + B);
+    static constexpr size_t SMEM = (size_t)STAGES * (A + B) + sizeof(Bars) + 1024;
+};
+
+int g_num_sms = 0;
+
+template <int BN, int CK>
+int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+    using C = Cfg<BN, CK>;
+    auto kern = conv_tc_kernel<BN, CK, C::STAGES>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int grid = p.num_tiles < g_num_sms ? p.num_tiles : g_num_sms;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+int dispatch(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+#define FVV_CASE(BN_, CK_) \
+    if (bn == BN_ && ck == CK_) return launch_cfg<BN_, CK_>(ma, mb, p, st);
+    FVV_CASE(16, 16) FVV_CASE(16, 64) FVV_CASE(32, 16) FVV_CASE(32, 32) FVV_CASE(32, 64)
+    FVV_CASE(64, 32) FVV_CASE(64, 64) FVV_CASE(128, 16) FVV_CASE(128, 32) FVV_CASE(128, 64)
+    FVV_CASE(256, 64)
+#undef FVV_CASE
+    set_error("no tensor-core kernel for N=%d, CK=%d", bn, ck);
     return FVV_EINVAL;
 }
-int tc_conv(fvv_interp *, int, const void *, int, int, int, int, int, void *, int, int, bool, cudaStream_t) {
-    set_error("tensor-core path not built");
-    return FVV_EINVAL;
+
+} // namespace
+
+// Pack every layer's weights as bf16 [G][Co_pad][Ci_pad] (G = 9 taps, or 4 phases
+// x 4 taps for the transposed conv) and build its B tensor map.
+int tc_prepare(fvv_interp *h, const float *blob) {
+    FVV_TRY(get_encoder());
+    if (h->o.pad_mode != FVV_PAD_ZERO) {
+        set_error("the tensor-core path supports zero padding only (circular mode runs in FP32)");
+        return FVV_EINVAL;
+    }
+    size_t off = 0;
+    for (int i = 0; i < kNumLayers; ++i) {
+        const LayerDef &L = kLayers[i];
+        int taps = L.kind == K_CONV ? 9 : 16;
+        int cip = ci_pad_of(L.ci), cop = pad16(L.co);
+        const float *w = blob + off;
+        off += (size_t)L.ci * L.co * taps + L.co;
+        std::vector<bf16> pk((size_t)taps * cop * cip, __float2bfloat16_rn(0.f));
+        if (L.kind == K_CONV) {
+            for (int tap = 0; tap < 9; ++tap)
+                for (int co = 0; co < L.co; ++co)
+                    for (int ci = 0; ci < L.ci; ++ci)
+                        pk[((size_t)tap * cop + co) * cip + ci] = __float2bfloat16_rn(w[((size_t)co * L.ci + ci) * 9 + tap]);
+        } else {
+            for (int py = 0; py < 2; ++py)
+                for (int px = 0; px < 2; ++px)
+                    for (int ty = 0; ty < 2; ++ty)
+                        for (int tx = 0; tx < 2; ++tx) {
+                            int ky = py == 0 ? 1 + 2 * ty : 2 * ty, kx = px == 0 ? 1 + 2 * tx : 2 * tx;
+                            int g = (py * 2 + px) * 4 + ty * 2 + tx;
+                            for (int co = 0; co < L.co; ++co)
+                                for (int ci = 0; ci < L.ci; ++ci)
+                                    pk[((size_t)g * cop + co) * cip + ci] =
+                                        __float2bfloat16_rn(w[((size_t)ci * L.co + co) * 16 + ky * 4 + kx]);
+                        }
+        }
+        TcWeights &tw = h->tc[i];
+        tw.ci_pad = cip;
+        tw.co_pad = cop;
+        FVV_TRY(dalloc(h, &tw.w, pk.size() * 2));
+        FVV_CHECK_CUDA(cudaMemcpy(tw.w, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice));
+        int ck = ck_of(cip);
+        cuuint64_t dims[3] = {(cuuint64_t)cip, (cuuint64_t)cop, (cuuint64_t)taps};
+        cuuint64_t strides[2] = {(cuuint64_t)cip * 2, (cuuint64_t)cip * cop * 2};
+        cuuint32_t box[3] = {(cuuint32_t)ck, (cuuint32_t)cop, 1};
+        static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+        FVV_TRY(encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, ck * 2));
+    }
+    return FVV_OK;
 }
+
+int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win, void *out,
+            int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
+    const LayerDef &L = kLayers[li];
+    const TcWeights &tw = h->tc[li];
+    const int cip = tw.ci_pad, ck = ck_of(cip), bn = tw.co_pad;
+    if (in_cs % 8 || in_coff % 8 || in_coff + cip > in_cs) {
+        set_error("layer %s: input slice (cs %d, off %d, %d ch) not TMA-aligned", L.name, in_cs, in_coff, cip);
+        return FVV_EINVAL;
+    }
+    TcParams p{};
+    p.mode = L.kind == K_CONVT ? MODE_T : (L.stride == 2 ? MODE_S2 : MODE_S1);
+    p.n_img = N;
+    if (L.kind == K_CONV) { p.gh = (Hin - 1) / L.stride + 1; p.gw = (Win - 1) / L.stride + 1; }
+    else { p.gh = Hin; p.gw = Win; }
+    p.out_h = L.kind == K_CONV ? p.gh : 2 * Hin;
+    p.out_w = L.kind == K_CONV ? p.gw : 2 * Win;
+    Shape s = pick_shape(p.gh, p.gw);
+    p.th_log = s.th_log; p.tw_log = s.tw_log;
+    p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
+    p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
+    long long tiles = (long long)N * p.tiles_y * p.tiles_x * (p.mode == MODE_T ? 4 : 1);
+    if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
+    p.num_tiles = (int)tiles;
+    p.nck = cip / ck;
+    p.taps = L.kind == K_CONV ? 9 : 4;
+    p.in_cs = in_cs; p.in_coff = in_coff;
+    p.co = L.co; p.relu = L.relu; p.out_f32 = out_f32 ? 1 : 0;
+    p.out = out; p.out_cs = out_cs; p.out_coff = out_coff;
+    p.bias = h->bias + h->b_off[li];
+    p.err = h->d_err;
+
+    CUtensorMap ma;
+    const int tw_ = 1 << s.tw_log, th_ = 1 << s.th_log;
+    if (p.mode == MODE_S2) {
+        if (Hin % 2 || Win % 2) { set_error("stride-2 layer %s needs even input size", L.name); return FVV_ESHAPE; }
+        cuuint64_t dims[5] = {(cuuint64_t)2 * in_cs, (cuuint64_t)Win / 2, 2, (cuuint64_t)Hin / 2, (cuuint64_t)N};
+        cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * 2, (cuuint64_t)Win * in_cs * 2,
+                                 (cuuint64_t)2 * Win * in_cs * 2, (cuuint64_t)Hin * Win * in_cs * 2};
+        cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)tw_, 1, (cuuint32_t)th_, 1};
+        FVV_TRY(encode(&ma, 5, (void *)in, dims, strides, box, ck * 2));
+    } else {
+        cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
+        cuuint64_t strides[3] = {(cuuint64_t)in_cs * 2, (cuuint64_t)Win * in_cs * 2, (cuuint64_t)Hin * Win * in_cs * 2};
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)tw_, (cuuint32_t)th_, 1};
+        FVV_TRY(encode(&ma, 4, (void *)in, dims, strides, box, ck * 2));
+    }
+    return dispatch(bn, ck, ma, *(const CUtensorMap *)tw.map, p, st);
+}
+
 } // namespace fvv

@@ -23,6 +23,7 @@ size_t blob_floats();
 struct TcWeights {
     void *w = nullptr;      // device, [phase*taps][Co_pad][Ci_pad] bf16 (or fp8) K-major
     float *scale = nullptr; // FP8: per-output-channel dequantisation scale
+    alignas(64) unsigned char map[128] = {}; // host CUtensorMap of w (B operand)
     int ci_pad = 0, co_pad = 0;
 };
 
