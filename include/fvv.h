@@ -116,6 +116,24 @@ int fvv_interp_last_launches(const fvv_interp *h);
  * otherwise).  For tests and debugging; not needed on the product path. */
 int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_floats);
 
+/* Run one layer of Table 3 (index 0..50, blob order) alone on caller buffers,
+ * with the handle's weights and precision: a 3x3 pad-1 conv (stride 1 or 2) or
+ * a 4x4 stride-2 pad-1 transposed conv, + bias, + ReLU where Table 3 has one.
+ * in: DEVICE, n x H x W pixels, pixel stride in_cs elements, the layer's C_in
+ *   channels starting at in_coff; float32 on the FP32 path, bfloat16 otherwise
+ *   (then in_cs, in_coff multiples of 8 and, for C_in < 16 or 17..31, the
+ *   channels up to 16 / 32 readable, their weights being zero).
+ * out: DEVICE, n x Ho x Wo pixels, pixel stride out_cs, written at out_coff;
+ *   float32 if out_f32 or on the FP32 path, else bfloat16.
+ * Asynchronous on `stream`.  Used by the kernel-level tests. */
+int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int n, int H, int W,
+                     void *out, int out_cs, int out_coff, int out_f32, void *stream);
+
+/* Synchronise the device and report whether any bounded device-side wait of
+ * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
+ * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */
+int fvv_interp_status(fvv_interp *h);
+
 /* Per-layer timing (the analogue of the paper's per-module latency, Table 2).
  * fvv_interp_profile(h, 1) brackets every convolution launch of later runs with
  * CUDA events on the run's stream (small overhead); 0 turns it off.  Both reset

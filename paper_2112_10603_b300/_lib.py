@@ -59,6 +59,8 @@ def lib():
         L.fvv_interp_device_bytes.restype = ctypes.c_size_t
         L.fvv_interp_last_launches.argtypes = [_P]
         L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
+        L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
+        L.fvv_interp_status.argtypes = [_P]
         L.fvv_interp_profile.argtypes = [_P, ctypes.c_int]
         L.fvv_interp_layer_stats.argtypes = [_P, _P, _P, _P, ctypes.c_int]
         L.fvv_interp_destroy.argtypes = [_P]
@@ -164,6 +166,16 @@ def fvv_interp_peek(h: int, which: int, view: int, shape):
     out = np.empty(shape, np.float32)
     _check(lib().fvv_interp_peek(h, which, view, out.ctypes.data, out.size))
     return out
+
+
+def fvv_interp_layer(h: int, layer: int, inp, in_cs: int, in_coff: int, n: int, H: int, W: int,
+                     out, out_cs: int, out_coff: int, out_f32: bool, stream=None):
+    _check(lib().fvv_interp_layer(h, layer, _dev(inp), in_cs, in_coff, n, H, W, _dev(out), out_cs, out_coff,
+                                  int(out_f32), _stream(stream)))
+
+
+def fvv_interp_status(h: int):
+    _check(lib().fvv_interp_status(h))
 
 
 def fvv_interp_profile(h: int, enable: bool):

@@ -45,7 +45,7 @@ struct TcParams {
     int taps;               // 9 (conv) or 4 (convT phase)
     int in_cs, in_coff;     // input pixel stride / channel offset (elements)
     int co;                 // real output channels
-    int relu, out_f32;
+    int relu, out_f32, vec_ok;
     void *out;
     int out_cs, out_coff, out_h, out_w;
     const float *bias;
@@ -256,7 +256,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         if (c + j < p.co) dst[j] = v[j];
                 } else {
                     bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + c;
-                    if (c + 16 <= p.co) {
+                    if (c + 16 <= p.co && p.vec_ok) {
                         uint4 w0, w1;
                         __nv_bfloat162 h[8];
 #pragma unroll
@@ -460,6 +460,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.taps = L.kind == K_CONV ? 9 : 4;
     p.in_cs = in_cs; p.in_coff = in_coff;
     p.co = L.co; p.relu = L.relu; p.out_f32 = out_f32 ? 1 : 0;
+    p.vec_ok = (out_cs % 8 == 0 && out_coff % 8 == 0 && ((uintptr_t)out % 16) == 0) ? 1 : 0;
     p.out = out; p.out_cs = out_cs; p.out_coff = out_coff;
     p.bias = h->bias + h->b_off[li];
     p.err = h->d_err;

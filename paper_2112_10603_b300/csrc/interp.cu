@@ -438,6 +438,34 @@ int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_flo
     return FVV_OK;
 }
 
+int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int n, int H, int W,
+                     void *out, int out_cs, int out_coff, int out_f32, void *stream) {
+    clear_error();
+    if (!h || !in || !out || layer < 0 || layer >= kNumLayers) { set_error("bad layer arguments"); return FVV_EINVAL; }
+    const LayerDef &L = kLayers[layer];
+    if (n < 1 || H < 1 || W < 1 || in_coff < 0 || out_coff < 0 || in_cs < in_coff + L.ci || out_cs < out_coff + L.co) {
+        set_error("layer %s: bad sizes", L.name); return FVV_ESHAPE;
+    }
+    if (L.kind == K_CONV && L.stride == 2 && (H % 2 || W % 2)) { set_error("stride-2 layer needs even H, W"); return FVV_ESHAPE; }
+    g_launches = 0;
+    return conv(h, layer, in, in_cs, in_coff, n, H, W, out, out_cs, out_coff, out_f32 != 0 || !is_bf16(h),
+                (cudaStream_t)stream);
+}
+
+int fvv_interp_status(fvv_interp *h) {
+    clear_error();
+    if (!h) { set_error("NULL handle"); return FVV_EINVAL; }
+    FVV_CHECK_CUDA(cudaDeviceSynchronize());
+    int err = 0;
+    FVV_CHECK_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+        set_error("a bounded device wait gave up (code %d)", err);
+        return FVV_ETIMEOUT;
+    }
+    return FVV_OK;
+}
+
 static void prof_reset(fvv_interp *h) {
     for (auto &r : h->prof) { h->ev_pool.push_back(r.a); h->ev_pool.push_back(r.b); }
     h->prof.clear();

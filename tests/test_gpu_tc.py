@@ -1,0 +1,94 @@
+"""GPU parity of the tcgen05 BF16 tensor-core path.
+
+Kernel level: every layer of Table 3 run alone (fvv_interp_layer) on ragged
+sizes that span several 128-pixel tiles, against the oracle's conv of the SAME
+bf16-rounded input and weights in FP64.  Products of two bf16 values are exact
+in FP32, so the only difference is FP32 summation order: the bar is
+|err| <= 2e-5 * (sum of |terms| bound) ~ 1e-4 relative to the output scale.
+Network level: the BF16 forward against the FP64 oracle, max error and PSNR.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2112_10603_b300 as fvv
+from synth import weights
+from tests.gpu_common import blob, oracle_view, pair, psnr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    return torch
+
+
+def _bf16_round(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _ci_pad(ci):
+    return 16 if ci <= 16 else (32 if ci <= 32 else (ci + 63) // 64 * 64)
+
+
+LAYERS = weights.manifest()
+
+
+@pytest.mark.parametrize("li", range(len(LAYERS)), ids=[m[0] for m in LAYERS])
+def test_layer_matches_oracle_conv(torch_cuda, li):
+    torch = torch_cuda
+    name, kind, ci, co, stride, relu = LAYERS[li]
+    rng = np.random.default_rng(100 + li)
+    # input sizes: ragged w.r.t. every tile shape; stride-2 layers need even sizes
+    H, W = (20, 38) if kind == "convT" else ((36, 70) if stride == 2 else (37, 70))
+    n = 2
+    cs = _ci_pad(ci) + (8 if li % 3 == 0 else 0)   # sometimes a wider pixel stride
+    coff = 8 if li % 3 == 0 else 0
+    x = np.zeros((n, H, W, cs), np.float32)
+    x[..., coff:coff + ci] = rng.standard_normal((n, H, W, ci)) * 0.5
+    x = _bf16_round(torch, x)
+    wv, bv = weights.layer_views(blob())[name]
+    wq = _bf16_round(torch, wv)
+    it = fvv.Interpolator(blob(), 64, 64, precision=fvv.FVV_BF16, max_views=1)
+    Ho, Wo = (2 * H, 2 * W) if kind == "convT" else ((H - 1) // stride + 1, (W - 1) // stride + 1)
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    out = torch.full((n, Ho, Wo, co + 3), -7.0, dtype=torch.float32, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, cs, coff, n, H, W, out, co + 3, 2, True)
+    outb = torch.zeros((n, Ho, Wo, co), dtype=torch.bfloat16, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, cs, coff, n, H, W, outb, co, 0, False)
+    fvv.fvv_interp_status(it.h)
+    got = out.cpu().numpy()
+    gotb = outb.to(torch.float32).cpu().numpy()
+    assert (got[..., :2] == -7).all() and (got[..., 2 + co:] == -7).all(), "wrote outside its channel slot"
+    for i in range(n):
+        xi = x[i, ..., coff:coff + ci]
+        if kind == "conv":
+            ref = oracle.conv3x3(xi, wq, bv, stride=stride, relu=relu)
+        else:
+            ref = oracle.conv_transpose4x4(xi, wq, bv, relu=relu)
+        scale = max(1.0, float(np.abs(ref).max()))
+        err = np.abs(got[i, ..., 2:2 + co] - ref).max()
+        assert err <= 1e-4 * scale, (name, i, err, scale)
+        errb = np.abs(gotb[i] - ref).max()
+        assert errb <= 8e-3 * scale, (name, i, errb, scale)
+
+
+def test_bf16_network_256(torch_cuda):
+    torch = torch_cuda
+    H = W = 256
+    left, right = pair(1, H, W, 12.0)
+    ref, dumps = oracle_view(1, H, W, 12.0, 0.5)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=2)
+    out = it.run(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), [0.5, 0.25]).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    p = psnr(out[0], ref)
+    err = float(np.abs(out[0] - ref).max())
+    print(f"BF16 256x256: PSNR {p:.2f} dB, max err {err:.4f}")
+    flow_err = np.abs(it.peek("vib2") - dumps["vib2"]).max()
+    print(f"BF16 256x256: stage-2 flow/mask max err {flow_err:.4f}")
+    assert np.isfinite(out).all()
+    assert p >= 38.0, p
