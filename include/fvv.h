@@ -122,7 +122,8 @@ int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_flo
  * in: DEVICE, n x H x W pixels, pixel stride in_cs elements, the layer's C_in
  *   channels starting at in_coff; float32 on the FP32 path, bfloat16 otherwise
  *   (then in_cs, in_coff multiples of 8 and, for C_in < 16 or 17..31, the
- *   channels up to 16 / 32 readable, their weights being zero).
+ *   channels up to 16 / 32 readable, their weights being zero).  ContextNet's
+ *   first layer (index 30, 3 input channels) always takes float32 input.
  * out: DEVICE, n x Ho x Wo pixels, pixel stride out_cs, written at out_coff;
  *   float32 if out_f32 or on the FP32 path, else bfloat16.
  * Asynchronous on `stream`.  Used by the kernel-level tests. */

@@ -140,7 +140,61 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(ConvArgs a) {
     }
 }
 
+// ContextNet's first layer (Table 3: Conv2d stride 2, 3 -> 16 channels) read
+// straight from the FP32 frame: one thread per output pixel keeps all 16
+// accumulators; the 27 x 16 weights sit in shared memory.  Same per-output
+// summation order as the GEMM kernel (tap, then input channel).
+template <typename Tout>
+__global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
+    __shared__ float ws[27 * 16];
+    __shared__ float bs[16];
+    const float *wp = static_cast<const float *>(a.w);
+    for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x) ws[i] = wp[i];
+    if (threadIdx.x < 16) bs[threadIdx.x] = a.bias[threadIdx.x];
+    __syncthreads();
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)a.N * a.Ho * a.Wo) return;
+    int ox = idx % a.Wo;
+    long long r = idx / a.Wo;
+    int oy = r % a.Ho, n = r / a.Ho;
+    const float *in = static_cast<const float *>(a.in);
+    float acc[16];
+#pragma unroll
+    for (int co = 0; co < 16; ++co) acc[co] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        int iy = wrap_or_mark(oy * a.stride + tap / 3 - 1, a.H, a.circ);
+        int ix = wrap_or_mark(ox * a.stride + tap % 3 - 1, a.W, a.circ);
+        if (iy < 0 || ix < 0) continue;
+        const float *src = in + ((size_t)(n * a.H + iy) * a.W + ix) * a.in_cs + a.in_coff;
+#pragma unroll
+        for (int ci = 0; ci < 3; ++ci) {
+            float v = __ldg(src + ci);
+#pragma unroll
+            for (int co = 0; co < 16; ++co) acc[co] = fmaf(v, ws[(tap * 3 + ci) * 16 + co], acc[co]);
+        }
+    }
+    Tout *dst = static_cast<Tout *>(a.out) + idx * a.out_cs + a.out_coff;
+#pragma unroll
+    for (int co = 0; co < 16; ++co) {
+        float v = acc[co] + bs[co];
+        store_out(dst + co, a.relu ? fmaxf(v, 0.f) : v);
+    }
+}
+
 } // namespace
+
+int launch_conv_c3(const ConvArgs &a, bool out_bf16, cudaStream_t st) {
+    if (a.Ci != 3 || a.Co != 16 || a.kind != K_CONV) { set_error("conv_c3: 3 -> 16 conv only"); return FVV_EINVAL; }
+    long long n = (long long)a.N * a.Ho * a.Wo;
+    if (n <= 0) return FVV_OK;
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    if (out_bf16) conv_c3_kernel<bf16><<<blocks, 256, 0, st>>>(a);
+    else conv_c3_kernel<float><<<blocks, 256, 0, st>>>(a);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
 
 int launch_conv_simt(const ConvArgs &a, bool in_bf16, bool out_bf16, cudaStream_t st) {
     const bool convt = a.kind == K_CONVT;

@@ -26,13 +26,17 @@
 #include <vector>
 
 #include "interp.h"
+#include "sampling.h"
 #include "tc_ptx.h"
 
 namespace fvv {
 
 namespace {
 
-enum { MODE_S1 = 0, MODE_S2 = 1, MODE_T = 2 };
+// MODE_T3: a transposed conv with few output channels computed for all 4 output
+// phases at once as a 3x3 conv over the input grid with N = 4 x C_out (phase-major
+// columns; each phase's weights are zero on the 5 taps it does not use).
+enum { MODE_S1 = 0, MODE_S2 = 1, MODE_T = 2, MODE_T3 = 3 };
 constexpr int kThreads = 192;
 constexpr long long kWaitCycles = 4000000000ll; // ~2 s: far beyond any legitimate wait
 
@@ -42,14 +46,15 @@ struct TcParams {
     int th_log, tw_log;     // tile = (1 << th_log) x (1 << tw_log) = 128 pixels
     int tiles_y, tiles_x, num_tiles;
     int nck;                // channel blocks per tap
-    int taps;               // 9 (conv) or 4 (convT phase)
+    int taps;               // 9 (conv, MODE_T3) or 4 (convT phase)
     int in_cs, in_coff;     // input pixel stride / channel offset (elements)
-    int co;                 // real output channels
+    int co;                 // real output channels (per phase in MODE_T3)
     int relu, out_f32, vec_ok;
     void *out;
     int out_cs, out_coff, out_h, out_w;
     const float *bias;
     int *err;
+    TcEpi epi;
 };
 
 struct __align__(8) Bars {
@@ -87,8 +92,35 @@ __device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase
     x0 = tx << p.tw_log;
 }
 
-template <int BN, int CK, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+// One output element of the epilogue (scalar path): bias, ReLU, then store, or
+// the fused Eq. 2 update, or the fused residual output.
+__device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int ox, int co, float acc) {
+    float x = acc + __ldg(p.bias + co);
+    if (p.relu) x = fmaxf(x, 0.f);
+    size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
+    if (p.epi.mode == EPI_RESID) {
+        // F^s, M^s = up(F^{s-1}) x 2, up(M^{s-1}) + Res^s; previous stage on the half grid
+        int h2 = p.out_h / 2, w2 = p.out_w / 2;
+        const float *fm = p.epi.fm_prev + (size_t)n * h2 * w2 * 5;
+        Taps u = up_taps(ox, oy, h2, w2, 0);
+        x += bilerp(fm, 5, co, u) * (co < 4 ? 2.f : 1.f);
+        ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
+    } else if (p.epi.mode == EPI_OUTPUT) {
+        // clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to the caller's H x W
+        if (oy < p.epi.crop_h && ox < p.epi.crop_w) {
+            float r = 2.f * sigmoidf_(x) - 1.f;
+            float v = fminf(fmaxf(p.epi.ib[pix * 3 + co] + r, 0.f), 1.f);
+            p.epi.final_out[(((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3 + co] = v;
+        }
+    } else if (p.out_f32) {
+        ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
+    } else {
+        ((bf16 *)p.out)[pix * p.out_cs + p.out_coff + co] = __float2bfloat16_rn(x);
+    }
+}
+
+template <int BN, int CK, int STAGES, int CTAS>
+__global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
     constexpr uint32_t A_BYTES = 128 * CK * 2, B_BYTES = BN * CK * 2;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
@@ -146,7 +178,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     uint32_t fb = ptx::smem_u32(&bars->full[stage]);
                     ptx::mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES);
                     uint32_t da = ptx::smem_u32(sA + stage * A_STRIDE), db = ptx::smem_u32(sB + stage * B_STRIDE);
-                    if (p.mode == MODE_S1) {
+                    if (p.mode == MODE_S1 || p.mode == MODE_T3) {
                         int ky = tap / 3, kx = tap - 3 * (tap / 3);
                         ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1, y0 + ky - 1, n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
@@ -227,51 +259,117 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
             tile_coords(p, t, ph, n, y0, x0);
-            if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
-            ptx::tc_fence_after();
             int gy = y0 + dy, gx = x0 + dx;
             bool valid = gy < p.gh && gx < p.gw;
-            int oy = gy, ox = gx;
-            if (p.mode == MODE_T) { oy = 2 * gy + (ph >> 1); ox = 2 * gx + (ph & 1); }
-            size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+            if (BN == 32 && p.epi.mode == EPI_RESID) {
+                // Eq. 2 update of a 4-phase transposed conv with 5 outputs (the VIB
+                // t1 layer): this pixel q of the half grid owns the 4 fine pixels
+                // (2q + phase); their x2 upsampling reads the 3x3 neighbourhood of q
+                // in the previous stage's F, M, fetched before the accumulator is ready.
+                float nb[3][3][5];
+                const int h2 = p.gh, w2 = p.gw;
+                const float *fm = p.epi.fm_prev + (size_t)n * h2 * w2 * 5;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        int yy = min(max(gy + a - 1, 0), h2 - 1), xx = min(max(gx + b - 1, 0), w2 - 1);
+                        const float *src = fm + ((size_t)yy * w2 + xx) * 5;
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) nb[a][b][k] = valid ? __ldg(src + k) : 0.f;
+                    }
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
+                ptx::tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    uint32_t r[16];
+                    __syncwarp();
+                    ptx::tmem_ld16(tbase + c, r);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = c + j, pj = col / 5, co = col % 5, py = pj >> 1, px = pj & 1;
+                        if (col < 20 && valid) {
+                            const float ly = py ? 0.25f : 0.75f, lx = px ? 0.25f : 0.75f;
+                            float up = (1.f - ly) * ((1.f - lx) * nb[py][px][co] + lx * nb[py][px + 1][co]) +
+                                       ly * ((1.f - lx) * nb[py + 1][px][co] + lx * nb[py + 1][px + 1][co]);
+                            float x = __uint_as_float(r[j]) + __ldg(p.bias + co) + up * (co < 4 ? 2.f : 1.f);
+                            size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
+                            ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
+                        }
+                    }
+                }
+            } else if (BN == 16 && p.epi.mode == EPI_OUTPUT) {
+                // residual output fused into the 16 -> 3 conv: I_blend fetched early
+                const bool in_crop = valid && gy < p.epi.crop_h && gx < p.epi.crop_w;
+                size_t pix = ((size_t)n * p.out_h + gy) * p.out_w + gx;
+                float ibv[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) ibv[k] = in_crop ? __ldg(p.epi.ib + pix * 3 + k) : 0.f;
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
+                ptx::tc_fence_after();
+                uint32_t r[16];
+                __syncwarp();
+                ptx::tmem_ld16(tbase, r);
+                ptx::tmem_ld_wait();
+                if (in_crop) {
+                    float *dst = p.epi.final_out + (((size_t)n * p.epi.crop_h + gy) * p.epi.crop_w + gx) * 3;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        float z = __uint_as_float(r[k]) + __ldg(p.bias + k);
+                        dst[k] = fminf(fmaxf(ibv[k] + 2.f * sigmoidf_(z) - 1.f, 0.f), 1.f);
+                    }
+                }
+            } else {
+            if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
+            ptx::tc_fence_after();
+            const int ncols = p.mode == MODE_T3 ? 4 * p.co : p.co; // columns that hold outputs
 #pragma unroll 1
             for (int c = 0; c < BN; c += 16) {
                 uint32_t r[16];
                 __syncwarp();
                 ptx::tmem_ld16(tbase + c, r);
                 ptx::tmem_ld_wait();
-                if (valid) {
-                float v[16];
+                if (!valid || c >= ncols) continue;
+                // output pixel and channel of column c (a chunk never straddles a
+                // phase when C_out is a multiple of 16)
+                int cph = p.mode == MODE_T3 ? c / p.co : ph;
+                int co0 = p.mode == MODE_T3 ? c - cph * p.co : c;
+                int oy = gy, ox = gx;
+                if (p.mode == MODE_T || p.mode == MODE_T3) { oy = 2 * gy + (cph >> 1); ox = 2 * gx + (cph & 1); }
+                if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co) {
+                    __nv_bfloat162 h[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    int co = c + j;
-                    float x = __uint_as_float(r[j]) + (co < p.co ? __ldg(p.bias + co) : 0.f);
-                    v[j] = p.relu ? fmaxf(x, 0.f) : x;
-                }
-                if (p.out_f32) {
-                    float *dst = (float *)p.out + pix * p.out_cs + p.out_coff + c;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c + j < p.co) dst[j] = v[j];
+                    for (int j = 0; j < 8; ++j) {
+                        float a = __uint_as_float(r[2 * j]) + __ldg(p.bias + co0 + 2 * j);
+                        float b = __uint_as_float(r[2 * j + 1]) + __ldg(p.bias + co0 + 2 * j + 1);
+                        if (p.relu) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
+                        h[j] = __floats2bfloat162_rn(a, b);
+                    }
+                    size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
+                    uint4 w0, w1;
+                    memcpy(&w0, &h[0], 16);
+                    memcpy(&w1, &h[4], 16);
+                    bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + co0;
+                    reinterpret_cast<uint4 *>(dst)[0] = w0;
+                    reinterpret_cast<uint4 *>(dst)[1] = w1;
                 } else {
-                    bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + c;
-                    if (c + 16 <= p.co && p.vec_ok) {
-                        uint4 w0, w1;
-                        __nv_bfloat162 h[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        memcpy(&w0, &h[0], 16);
-                        memcpy(&w1, &h[4], 16);
-                        reinterpret_cast<uint4 *>(dst)[0] = w0;
-                        reinterpret_cast<uint4 *>(dst)[1] = w1;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c + j < p.co) dst[j] = __float2bfloat16_rn(v[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        if (c + j >= ncols) break;
+                        int col = c + j, pj = cph, co = col;
+                        int yy = oy, xx = ox;
+                        if (p.mode == MODE_T3) {
+                            pj = col / p.co;
+                            co = col - pj * p.co;
+                            yy = 2 * gy + (pj >> 1);
+                            xx = 2 * gx + (pj & 1);
+                        }
+                        epi_elem(p, n, yy, xx, co, __uint_as_float(r[j]));
                     }
                 }
-                }
+            }
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(ptx::smem_u32(&bars->tmem_empty[acc]));
@@ -342,10 +440,19 @@ Shape pick_shape(int gh, int gw) {
     return best;
 }
 
+// Resources of one (N tile, channel block) configuration.  Small-N configs put
+// several CTAs on an SM (their TMEM columns and shared memory allow it), so more
+// TMA copies are in flight per SM: those layers are bound by copy latency.
+constexpr uint32_t kSmemBudget = 220 * 1024; // per SM, for all resident CTAs
 template <int BN, int CK> struct Cfg {
     static constexpr uint32_t A = ((128 * CK * 2) + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
-    static constexpr int STAGES = (200 * 1024) / (A + B) > 8 ? 8 : (200 * 1024) / (A + B);
+    static constexpr uint32_t TMEM_COLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048) / (A + B)); }
+    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
+    static constexpr int CTAS = ctas_for((512 / TMEM_COLS) < 4 ? (512 / TMEM_COLS) : 4);
+    static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
     static constexpr size_t SMEM = (size_t)STAGES * (A + B) + sizeof(Bars) + 1024;
+    static_assert(STAGES >= 2 && CTAS * TMEM_COLS <= 512, "tensor-core config");
 };
 
 int g_num_sms = 0;
@@ -353,7 +460,7 @@ int g_num_sms = 0;
 template <int BN, int CK>
 int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
     using C = Cfg<BN, CK>;
-    auto kern = conv_tc_kernel<BN, CK, C::STAGES>;
+    auto kern = conv_tc_kernel<BN, CK, C::STAGES, C::CTAS>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -364,7 +471,8 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, 
         FVV_CHECK_CUDA(cudaGetDevice(&dev));
         FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    int grid = p.num_tiles < g_num_sms ? p.num_tiles : g_num_sms;
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
     kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, p);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());
@@ -395,16 +503,34 @@ int tc_prepare(fvv_interp *h, const float *blob) {
     size_t off = 0;
     for (int i = 0; i < kNumLayers; ++i) {
         const LayerDef &L = kLayers[i];
-        int taps = L.kind == K_CONV ? 9 : 16;
-        int cip = ci_pad_of(L.ci), cop = pad16(L.co);
+        const bool t3 = tc_all_phases(i);
+        int taps = L.kind == K_CONV || t3 ? 9 : 16;  // B slices: conv/all-phase taps, or phase x tap
+        int cip = ci_pad_of(L.ci), cop = pad16(t3 ? 4 * L.co : L.co);
         const float *w = blob + off;
-        off += (size_t)L.ci * L.co * taps + L.co;
+        off += (size_t)L.ci * L.co * (L.kind == K_CONV ? 9 : 16) + L.co;
         std::vector<bf16> pk((size_t)taps * cop * cip, __float2bfloat16_rn(0.f));
         if (L.kind == K_CONV) {
             for (int tap = 0; tap < 9; ++tap)
                 for (int co = 0; co < L.co; ++co)
                     for (int ci = 0; ci < L.ci; ++ci)
                         pk[((size_t)tap * cop + co) * cip + ci] = __float2bfloat16_rn(w[((size_t)co * L.ci + ci) * 9 + tap]);
+        } else if (t3) {
+            // tap (dy, dx) in {-1,0,1}^2 of phase (py, px): rows dy in {-1, 0} (py = 0,
+            // kernel rows 3, 1) or {0, 1} (py = 1, kernel rows 2, 0); same for columns
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int py = 0; py < 2; ++py)
+                        for (int px = 0; px < 2; ++px) {
+                            bool oky = py == 0 ? dy <= 0 : dy >= 0, okx = px == 0 ? dx <= 0 : dx >= 0;
+                            if (!oky || !okx) continue;
+                            int ky = py == 0 ? (dy == 0 ? 1 : 3) : (dy == 1 ? 0 : 2);
+                            int kx = px == 0 ? (dx == 0 ? 1 : 3) : (dx == 1 ? 0 : 2);
+                            int tap = (dy + 1) * 3 + (dx + 1), ph = py * 2 + px;
+                            for (int co = 0; co < L.co; ++co)
+                                for (int ci = 0; ci < L.ci; ++ci)
+                                    pk[((size_t)tap * cop + ph * L.co + co) * cip + ci] =
+                                        __float2bfloat16_rn(w[((size_t)ci * L.co + co) * 16 + ky * 4 + kx]);
+                        }
         } else {
             for (int py = 0; py < 2; ++py)
                 for (int px = 0; px < 2; ++px)
@@ -433,8 +559,10 @@ int tc_prepare(fvv_interp *h, const float *blob) {
     return FVV_OK;
 }
 
+bool tc_all_phases(int li) { return kLayers[li].kind == K_CONVT && 4 * kLayers[li].co <= 64; }
+
 int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win, void *out,
-            int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
+            int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi) {
     const LayerDef &L = kLayers[li];
     const TcWeights &tw = h->tc[li];
     const int cip = tw.ci_pad, ck = ck_of(cip), bn = tw.co_pad;
@@ -443,7 +571,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         return FVV_EINVAL;
     }
     TcParams p{};
-    p.mode = L.kind == K_CONVT ? MODE_T : (L.stride == 2 ? MODE_S2 : MODE_S1);
+    p.mode = L.kind == K_CONVT ? (tc_all_phases(li) ? MODE_T3 : MODE_T) : (L.stride == 2 ? MODE_S2 : MODE_S1);
     p.n_img = N;
     if (L.kind == K_CONV) { p.gh = (Hin - 1) / L.stride + 1; p.gw = (Win - 1) / L.stride + 1; }
     else { p.gh = Hin; p.gw = Win; }
@@ -457,13 +585,21 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
     p.num_tiles = (int)tiles;
     p.nck = cip / ck;
-    p.taps = L.kind == K_CONV ? 9 : 4;
+    p.taps = p.mode == MODE_T ? 4 : 9;
     p.in_cs = in_cs; p.in_coff = in_coff;
     p.co = L.co; p.relu = L.relu; p.out_f32 = out_f32 ? 1 : 0;
     p.vec_ok = (out_cs % 8 == 0 && out_coff % 8 == 0 && ((uintptr_t)out % 16) == 0) ? 1 : 0;
     p.out = out; p.out_cs = out_cs; p.out_coff = out_coff;
     p.bias = h->bias + h->b_off[li];
     p.err = h->d_err;
+    if (epi) {
+        p.epi = *epi;
+        // the fused epilogues are written for the layers that use them
+        bool ok = (epi->mode == EPI_STORE) ||
+                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5) ||
+                  (epi->mode == EPI_OUTPUT && p.mode == MODE_S1 && L.co == 3 && bn == 16);
+        if (!ok) { set_error("layer %s: unsupported fused epilogue", L.name); return FVV_EINVAL; }
+    }
 
     CUtensorMap ma;
     const int tw_ = 1 << s.tw_log, th_ = 1 << s.th_log;

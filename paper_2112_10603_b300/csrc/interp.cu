@@ -97,13 +97,14 @@ static cudaEvent_t pool_event(fvv_interp *h) {
 }
 
 static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
-                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st);
+                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi);
 
 // One conv layer: FP32 SIMT on the FP32 path, tensor cores otherwise; bracketed
 // by events while profiling.
 static int conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
-                void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
-    if (!h->profiling) return conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+                void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr) {
+    if (!h->profiling)
+        return conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st, epi);
     const LayerDef &L = kLayers[li];
     fvv_interp::ProfRec r;
     r.layer = li;
@@ -112,16 +113,18 @@ static int conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, i
     r.a = pool_event(h);
     r.b = pool_event(h);
     FVV_CHECK_CUDA(cudaEventRecord(r.a, st));
-    int rc = conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+    int rc = conv_impl(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st, epi);
     FVV_CHECK_CUDA(cudaEventRecord(r.b, st));
     h->prof.push_back(r);
     return rc;
 }
 
 static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
-                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st) {
+                     void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi) {
     const LayerDef &L = kLayers[li];
-    if (is_bf16(h)) return tc_conv(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st);
+    // ContextNet's first layer reads the 3-channel FP32 frame: SIMT on every path
+    const bool simt = !is_bf16(h) || li == kCtx;
+    if (!simt) return tc_conv(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st, epi);
     ConvArgs a{};
     a.in = in; a.in_cs = in_cs; a.in_coff = in_coff;
     a.out = out; a.out_cs = out_cs; a.out_coff = out_coff;
@@ -131,10 +134,11 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
     a.kind = L.kind; a.stride = L.stride; a.relu = L.relu; a.circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
     if (L.kind == K_CONV) { a.Ho = (Hin - 1) / L.stride + 1; a.Wo = (Win - 1) / L.stride + 1; }
     else { a.Ho = 2 * Hin; a.Wo = 2 * Win; }
-    return launch_conv_simt(a, false, false, st);
+    if (li == kCtx) return launch_conv_c3(a, is_bf16(h) && !out_f32, st);
+    return launch_conv_simt(a, false, is_bf16(h) && !out_f32, st);
 }
 
-template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
+template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st) {
     const int Hp = h->Hp, Wp = h->Wp, circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
     const bool b16 = is_bf16(h);
     const int cx0 = b16 ? 16 : 7, cx1 = b16 ? 32 : 18, cu0 = b16 ? 16 : 6;
@@ -144,13 +148,12 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     for (int k = 0; k < 5; ++k) U[k] = (T *)h->u[k];
 
     // a0: pyramid of every camera
-    FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2,
-                             b16 ? h->img0b : nullptr, st));
+    FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
     // a1: ContextNet, batched over cameras
     {
         int hh = Hp, ww = Wp;
-        const void *cur = b16 ? (const void *)h->img0b : (const void *)h->img0;
-        int cur_cs = b16 ? 16 : 3;
+        const void *cur = h->img0; // FP32 frame: the 3-channel first layer runs on the SIMT kernel
+        int cur_cs = 3;
         const int C[4] = {16, 32, 64, 128};
         for (int k = 0; k < 4; ++k) {
             FVV_TRY(conv(h, kCtx + 2 * k, cur, cur_cs, 0, n_cams, hh, ww, h->ctxt, C[k], 0, false, st));
@@ -174,8 +177,16 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             T *tmp = src; src = dst; dst = tmp;
         }
         FVV_TRY(conv(h, base + 8, src, 256, 0, nv, hs / 4, ws / 4, ta, 128, 0, false, st));
-        FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st));
-        if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, hs, ws, circ, st));
+        if (b16 && s > 0) {
+            // Eq. 2 update fused into the last convT's epilogue
+            TcEpi e;
+            e.mode = EPI_RESID;
+            e.fm_prev = h->fm[s - 1];
+            FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st, &e));
+        } else {
+            FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st));
+            if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, hs, ws, circ, st));
+        }
     }
     // a5: final warp + blend
     FVV_TRY(launch_final_blend<T>(h->img0, h->fm[2], vt, nv, Hp, Wp, circ, U[0], cu0, h->ib, st));
@@ -209,14 +220,26 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             FVV_TRY(conv(h, kRef + 8 + k, U[lvl], ucs[lvl], 0, nv, hh, ww, dst, dst_cs, 0, false, st));
             hh *= 2; ww *= 2;
         }
-        FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st));
+        if (b16) {
+            // a8 fused into the output conv's epilogue
+            TcEpi e;
+            e.mode = EPI_OUTPUT;
+            e.ib = h->ib;
+            e.final_out = out;
+            e.crop_h = h->H;
+            e.crop_w = h->W;
+            FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st, &e));
+        } else {
+            FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st));
+            FVV_TRY(launch_output(h->ib, h->z, 3, nv, Hp, Wp, h->H, h->W, out, st));
+        }
     }
     return FVV_OK;
 }
 
-int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
+int interp_forward(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st) {
     g_launches = 0;
-    int rc = is_bf16(h) ? forward_t<bf16>(h, n_cams, nv, st) : forward_t<float>(h, n_cams, nv, st);
+    int rc = is_bf16(h) ? forward_t<bf16>(h, n_cams, nv, out, st) : forward_t<float>(h, n_cams, nv, out, st);
     h->last_launches = g_launches;
     return rc;
 }
@@ -245,17 +268,14 @@ static int create_impl(fvv_interp *h, const float *blob) {
         }
         FVV_TRY(dalloc_t(h, &h->bias, btot * 4));
         FVV_CHECK_CUDA(cudaMemcpy(h->bias, bias.data(), btot * 4, cudaMemcpyHostToDevice));
-        if (!b16) {
-            FVV_TRY(dalloc_t(h, &h->w32, wtot * 4));
-            FVV_CHECK_CUDA(cudaMemcpy(h->w32, packed.data(), wtot * 4, cudaMemcpyHostToDevice));
-        }
+        FVV_TRY(dalloc_t(h, &h->w32, wtot * 4));
+        FVV_CHECK_CUDA(cudaMemcpy(h->w32, packed.data(), wtot * 4, cudaMemcpyHostToDevice));
     }
     if (b16) FVV_TRY(tc_prepare(h, blob));
     // per-camera
     FVV_TRY(dalloc_t(h, &h->img0, C * P * 3 * 4));
     FVV_TRY(dalloc_t(h, &h->img1, C * P / 4 * 3 * 4));
     FVV_TRY(dalloc_t(h, &h->img2, C * P / 16 * 3 * 4));
-    if (b16) FVV_TRY(dalloc_t(h, &h->img0b, C * P * 16 * 2));
     const int ctxC[4] = {16, 32, 64, 128};
     for (int k = 0; k < 4; ++k) FVV_TRY(dalloc(h, &h->ctx[k], C * (P >> (2 * k + 2)) * ctxC[k] * es));
     FVV_TRY(dalloc(h, &h->ctxt, C * (P / 4) * 16 * es));
@@ -368,11 +388,7 @@ int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const f
     std::vector<int> cl(n_views, 0), cr(n_views, 1);
     const float *cams[2] = {left, right};
     FVV_TRY(upload_tables(h, cams, 2, cl.data(), cr.data(), t, n_views, st));
-    FVV_TRY(interp_forward(h, 2, n_views, st));
-    int launches = h->last_launches;
-    int rc = launch_output(h->ib, h->z, 3, n_views, h->Hp, h->Wp, h->H, h->W, out, st);
-    h->last_launches = launches + 1;
-    return rc;
+    return interp_forward(h, 2, n_views, out, st);
 }
 
 int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
@@ -415,11 +431,7 @@ int fvv_interp_run_batch(fvv_interp *h, const float *const *cams, int n_cams, co
         if (!cams[c]) { set_error("cams[%d] is NULL", c); return FVV_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     FVV_TRY(upload_tables(h, cams, n_cams, cl.data(), cr.data(), t, nv, st));
-    FVV_TRY(interp_forward(h, n_cams, nv, st));
-    int launches = h->last_launches;
-    int rc = launch_output(h->ib, h->z, 3, nv, h->Hp, h->Wp, h->H, h->W, out, st);
-    h->last_launches = launches + 1;
-    return rc;
+    return interp_forward(h, n_cams, nv, out, st);
 }
 
 int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_floats) {
@@ -430,6 +442,7 @@ int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_flo
     size_t P = (size_t)h->Hp * h->Wp;
     const float *src;
     size_t n;
+    if (which == 4 && is_bf16(h)) { set_error("z is fused into the output on the tensor-core path"); return FVV_EINVAL; }
     if (which < 3) { n = (P >> (2 * (2 - which))) * 5; src = h->fm[which]; }
     else { n = P * 3; src = which == 3 ? h->ib : h->z; }
     if (n_floats != n) { set_error("peek: tensor has %zu floats, got %zu", n, n_floats); return FVV_ESHAPE; }

@@ -19,6 +19,16 @@ constexpr int kVib0 = 0, kVib1 = 10, kVib2 = 20, kCtx = 30, kRef = 38;
 
 size_t blob_floats();
 
+// Fused epilogues of the tensor-core convolutions.
+enum { EPI_STORE = 0, EPI_RESID = 1, EPI_OUTPUT = 2 };
+struct TcEpi {
+    int mode = EPI_STORE;
+    const float *fm_prev = nullptr; // EPI_RESID: previous stage F, M (half grid, 5 ch FP32)
+    const float *ib = nullptr;      // EPI_OUTPUT: I_blend on the padded grid (3 ch FP32)
+    float *final_out = nullptr;     // EPI_OUTPUT: cropped n x crop_h x crop_w x 3 output
+    int crop_h = 0, crop_w = 0;
+};
+
 // Packed weights of one layer for the tensor-core kernels.
 struct TcWeights {
     void *w = nullptr;      // device, [phase*taps][Co_pad][Ci_pad] bf16 (or fp8) K-major
@@ -39,7 +49,6 @@ struct fvv_interp {
     fvv::TcWeights tc[fvv::kNumLayers];
     // per-camera buffers
     float *img0 = nullptr, *img1 = nullptr, *img2 = nullptr;
-    fvv::bf16 *img0b = nullptr;
     void *ctx[4] = {}, *ctxt = nullptr;
     // per-view buffers
     void *xb = nullptr, *ta = nullptr, *ma = nullptr, *mb = nullptr;
@@ -65,9 +74,10 @@ struct fvv_interp {
 };
 
 namespace fvv {
-int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st);
+int interp_forward(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st);
 int dalloc(fvv_interp *h, void **p, size_t bytes);
 int tc_prepare(fvv_interp *h, const float *blob);
 int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
-            void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st);
+            void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr);
+bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
 } // namespace fvv

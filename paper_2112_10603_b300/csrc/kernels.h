@@ -13,10 +13,12 @@ struct ViewTab {
 
 // FP32 SIMT implicit-GEMM conv / convT (weights packed by pack_simt).
 int launch_conv_simt(const ConvArgs &a, bool in_bf16, bool out_bf16, cudaStream_t st);
+// direct kernel for a 3 -> 16 channel conv read from FP32 (ContextNet's first layer)
+int launch_conv_c3(const ConvArgs &a, bool out_bf16, cudaStream_t st);
 void pack_simt(int kind, int Ci, int Co, const float *w, float *dst);
 
 int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float *img0,
-                     float *img1, float *img2, bf16 *img0_b16, cudaStream_t st);
+                     float *img1, float *img2, cudaStream_t st);
 template <typename T>
 int launch_vib0_input(const float *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st);
 template <typename T>

@@ -10,8 +10,11 @@
 //    centres), taps clamp or wrap; flow values are doubled;
 //  * stage images and the flow pyramid are box averages.
 // All coordinates, weights, flows and mask logits are FP32.
+#include <cstring>
+
 #include "common.h"
 #include "kernels.h"
+#include "sampling.h"
 
 namespace fvv {
 
@@ -20,110 +23,76 @@ namespace {
 template <typename T> __device__ __forceinline__ T to_store(float v);
 template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 to_store<bf16>(float v) { return __float2bfloat16_rn(v); }
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(bf16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ int fix_index(int i, int n, int circ) {
-    if (circ) { i %= n; return i < 0 ? i + n : i; }
-    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+// Store the N values of one pixel, zero-padded to cs channels.  The bf16
+// layouts keep cs a multiple of 8 so that every pixel is 16-byte aligned and is
+// written with 16-byte stores.
+template <int N> __device__ __forceinline__ void store_px(float *dst, const float (&v)[N], int cs) {
+    for (int c = 0; c < cs; ++c) dst[c] = c < N ? v[c] : 0.f;
 }
-
-// Bilinear tap set for a backward warp at integer pixel (x, y) with flow (fx, fy).
-struct Taps { int o00, o01, o10, o11; float lx, ly; };
-
-__device__ __forceinline__ Taps warp_taps(int x, int y, float fx, float fy, int H, int W, int circ) {
-    // beyond the border every tap clamps to the same pixel; this also maps NaN
-    // (fmaxf returns the other operand) to a finite value, keeping indices in range
-    float lim = circ ? 16777216.f : (float)(max(H, W) + 4);
-    fx = fminf(fmaxf(fx, -lim), lim);
-    fy = fminf(fmaxf(fy, -lim), lim);
-    float flx = floorf(fx), fly = floorf(fy);
-    Taps t;
-    t.lx = fx - flx;
-    t.ly = fy - fly;
-    int x0 = x + (int)flx, y0 = y + (int)fly;
-    int xa = fix_index(x0, W, circ), xb = fix_index(x0 + 1, W, circ);
-    int ya = fix_index(y0, H, circ), yb = fix_index(y0 + 1, H, circ);
-    t.o00 = ya * W + xa; t.o01 = ya * W + xb; t.o10 = yb * W + xa; t.o11 = yb * W + xb;
-    return t;
+template <int N> __device__ __forceinline__ void store_px(bf16 *dst, const float (&v)[N], int cs) {
+    for (int c0 = 0; c0 < cs; c0 += 8) {
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = c0 + 2 * j;
+            h[j] = __floats2bfloat162_rn(c < N ? v[c] : 0.f, c + 1 < N ? v[c + 1] : 0.f);
+        }
+        uint4 u;
+        memcpy(&u, h, 16);
+        *reinterpret_cast<uint4 *>(dst + c0) = u;
+    }
 }
-
-template <typename T>
-__device__ __forceinline__ float bilerp(const T *img, int cs, int c, const Taps &t) {
-    float a = to_f(img[(size_t)t.o00 * cs + c]), b = to_f(img[(size_t)t.o01 * cs + c]);
-    float d = to_f(img[(size_t)t.o10 * cs + c]), e = to_f(img[(size_t)t.o11 * cs + c]);
-    return (1.f - t.ly) * ((1.f - t.lx) * a + t.lx * b) + t.ly * ((1.f - t.lx) * d + t.lx * e);
-}
-
-// x2 upsampling taps of fine pixel (Y, X) on a coarse h x w grid.
-__device__ __forceinline__ Taps up_taps(int X, int Y, int h, int w, int circ) {
-    Taps t;
-    int x0 = (X >> 1) - ((X & 1) ? 0 : 1), y0 = (Y >> 1) - ((Y & 1) ? 0 : 1);
-    t.lx = (X & 1) ? 0.25f : 0.75f;
-    t.ly = (Y & 1) ? 0.25f : 0.75f;
-    int xa = fix_index(x0, w, circ), xb = fix_index(x0 + 1, w, circ);
-    int ya = fix_index(y0, h, circ), yb = fix_index(y0 + 1, h, circ);
-    t.o00 = ya * w + xa; t.o01 = ya * w + xb; t.o10 = yb * w + xa; t.o11 = yb * w + xb;
-    return t;
-}
-
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 
 // ---------------------------------------------------------------------------
-// a0: zero-pad each camera frame to Hp x Wp and build its 1/2 and 1/4 box pyramid.
-// One thread per 4x4 block of the padded frame.
+// a0: zero-pad each camera frame to Hp x Wp and build its 1/2 box level.
+// One thread per 2x2 block (= one pixel of the 1/2 level).
 __global__ void prep_cams_kernel(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp,
-                                 float *img0, float *img1, float *img2, bf16 *img0_b16) {
-    int h4 = Hp / 4, w4 = Wp / 4;
+                                 float *img0, float *img1) {
+    int h2 = Hp / 2, w2 = Wp / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long total = (long long)n_cams * h4 * w4;
-    if (idx >= total) return;
-    int x4 = idx % w4;
-    long long r = idx / w4;
-    int y4 = r % h4, c = r / h4;
+    if (idx >= (long long)n_cams * h2 * w2) return;
+    int x2 = idx % w2;
+    long long r = idx / w2;
+    int y2 = r % h2, c = r / h2;
     const float *src = cams[c];
-    float blk[4][4][3];
-#pragma unroll
-    for (int dy = 0; dy < 4; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 4; ++dx) {
-            int y = y4 * 4 + dy, x = x4 * 4 + dx;
-            bool in = y < H && x < W;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) blk[dy][dx][ch] = in ? __ldg(src + ((size_t)y * W + x) * 3 + ch) : 0.f;
-        }
+    float s[3] = {0.f, 0.f, 0.f};
     size_t P0 = (size_t)Hp * Wp;
 #pragma unroll
-    for (int dy = 0; dy < 4; ++dy)
+    for (int dy = 0; dy < 2; ++dy) {
+        int y = 2 * y2 + dy;
+        float v[6];
 #pragma unroll
-        for (int dx = 0; dx < 4; ++dx) {
-            size_t p = (size_t)c * P0 + (size_t)(y4 * 4 + dy) * Wp + x4 * 4 + dx;
+        for (int dx = 0; dx < 2; ++dx) {
+            int x = 2 * x2 + dx;
+            bool in = y < H && x < W;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) img0[p * 3 + ch] = blk[dy][dx][ch];
-            if (img0_b16) {
-                bf16 *d = img0_b16 + p * 16;
-#pragma unroll
-                for (int ch = 0; ch < 16; ++ch) d[ch] = __float2bfloat16_rn(ch < 3 ? blk[dy][dx][ch] : 0.f);
-            }
+            for (int ch = 0; ch < 3; ++ch) v[3 * dx + ch] = in ? __ldg(src + ((size_t)y * W + x) * 3 + ch) : 0.f;
         }
-    size_t P1 = P0 / 4;
-    float s4[3] = {0.f, 0.f, 0.f};
+        float *d = img0 + ((size_t)c * P0 + (size_t)y * Wp + 2 * x2) * 3;
 #pragma unroll
-    for (int by = 0; by < 2; ++by)
+        for (int k = 0; k < 6; ++k) d[k] = v[k];
 #pragma unroll
-        for (int bx = 0; bx < 2; ++bx) {
-            size_t p = (size_t)c * P1 + (size_t)(y4 * 2 + by) * (Wp / 2) + x4 * 2 + bx;
+        for (int ch = 0; ch < 3; ++ch) s[ch] += v[ch] + v[3 + ch];
+    }
+    float *d1 = img1 + ((size_t)c * (P0 / 4) + (size_t)y2 * w2 + x2) * 3;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float s = blk[2 * by][2 * bx][ch] + blk[2 * by][2 * bx + 1][ch] +
-                          blk[2 * by + 1][2 * bx][ch] + blk[2 * by + 1][2 * bx + 1][ch];
-                img1[p * 3 + ch] = s * 0.25f;
-                s4[ch] += s;
-            }
-        }
-    size_t p2 = (size_t)c * (P0 / 16) + (size_t)y4 * w4 + x4;
+    for (int ch = 0; ch < 3; ++ch) d1[ch] = s[ch] * 0.25f;
+}
+
+// a0: the 1/4 level as the 2x2 box average of the 1/2 level (= the 4x4 box).
+__global__ void box_quarter_kernel(const float *img1, int n_cams, int h2, int w2, float *img2) {
+    int h4 = h2 / 2, w4 = w2 / 2;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_cams * h4 * w4) return;
+    int x = idx % w4;
+    long long r = idx / w4;
+    int y = r % h4, c = r / h4;
+    const float *s = img1 + (size_t)c * h2 * w2 * 3;
+    size_t p00 = ((size_t)(2 * y) * w2 + 2 * x) * 3, p10 = p00 + (size_t)w2 * 3;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) img2[p2 * 3 + ch] = s4[ch] * 0.0625f;
+    for (int ch = 0; ch < 3; ++ch)
+        img2[(size_t)idx * 3 + ch] = (s[p00 + ch] + s[p00 + 3 + ch] + s[p10 + ch] + s[p10 + 3 + ch]) * 0.25f;
 }
 
 // a2 input: [I_l/4, I_r/4, t] (7 channels, zero-padded to cs).
@@ -136,9 +105,8 @@ __global__ void vib0_input_kernel(const float *img2, const ViewTab vt, int nv, i
     long long p = idx % P;
     const float *L = img2 + ((size_t)vt.cam_l[v] * P + p) * 3;
     const float *R = img2 + ((size_t)vt.cam_r[v] * P + p) * 3;
-    T *d = x + (size_t)idx * cs;
     float vals[7] = {L[0], L[1], L[2], R[0], R[1], R[2], vt.t[v]};
-    for (int c = 0; c < cs; ++c) d[c] = to_store<T>(c < 7 ? vals[c] : 0.f);
+    store_px(x + (size_t)idx * cs, vals, cs);
 }
 
 // a3: stage s input [I_l, I_r, W_l, W_r, M_up, F_up(4), t] (18 ch, zero-padded to cs)
@@ -175,8 +143,7 @@ __global__ void stage_input_kernel(const float *imgs, const float *FMp, const Vi
 #pragma unroll
     for (int c = 0; c < 4; ++c) vals[13 + c] = up[c];
     vals[17] = vt.t[v];
-    T *d = x + (size_t)idx * cs;
-    for (int c = 0; c < cs; ++c) d[c] = to_store<T>(c < 18 ? vals[c] : 0.f);
+    store_px(x + (size_t)idx * cs, vals, cs);
 }
 
 // Eq. 2: F^s, M^s = up(F^{s-1}) x2, up(M^{s-1}) + Res^s  (in place on res).
@@ -211,15 +178,52 @@ __global__ void final_blend_kernel(const float *img0, const float *FM, const Vie
     Taps tl = warp_taps(X, Y, f[0], f[1], h, w, circ);
     Taps tr = warp_taps(X, Y, f[2], f[3], h, w, circ);
     float M = sigmoidf_(f[4]);
-    T *d = u0 + (size_t)idx * cs;
+    float vals[6];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float a = bilerp(L, 3, c, tl), b = bilerp(R, 3, c, tr);
-        d[c] = to_store<T>(a);
-        d[3 + c] = to_store<T>(b);
+        vals[c] = a;
+        vals[3 + c] = b;
         ib[(size_t)idx * 3 + c] = M * a + (1.f - M) * b;
     }
-    for (int c = 6; c < cs; ++c) d[c] = to_store<T>(0.f);
+    store_px(u0 + (size_t)idx * cs, vals, cs);
+}
+
+// Bilinear sample of 8 consecutive channels (bf16 storage, 16-byte loads).
+__device__ __forceinline__ void bilerp8(const bf16 *img, int cs, int c0, const Taps &t, float (&o)[8]) {
+    const int offs[4] = {t.o00, t.o01, t.o10, t.o11};
+    float a[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint4 u = __ldg(reinterpret_cast<const uint4 *>(img + (size_t)offs[k] * cs + c0));
+        __nv_bfloat162 hh[4];
+        memcpy(hh, &u, 16);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 f = __bfloat1622float2(hh[j]);
+            a[k][2 * j] = f.x;
+            a[k][2 * j + 1] = f.y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        o[j] = (1.f - t.ly) * ((1.f - t.lx) * a[0][j] + t.lx * a[1][j]) + t.ly * ((1.f - t.lx) * a[2][j] + t.lx * a[3][j]);
+}
+__device__ __forceinline__ void bilerp8(const float *img, int cs, int c0, const Taps &t, float (&o)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = bilerp(img, cs, c0 + j, t);
+}
+__device__ __forceinline__ void store8(float *d, const float (&v)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) d[j] = v[j];
+}
+__device__ __forceinline__ void store8(bf16 *d, const float (&v)[8]) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    uint4 u;
+    memcpy(&u, h, 16);
+    *reinterpret_cast<uint4 *>(d) = u;
 }
 
 // a6: flow pyramid level k: F_k = box2(F_{k-1}) / 2 (4 channels; F_0 = the final
@@ -257,12 +261,11 @@ __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, con
     Taps tl = warp_taps(X, Y, F[0], F[1], h, w, circ);
     Taps tr = warp_taps(X, Y, F[2], F[3], h, w, circ);
     T *d = dst + (size_t)vp * dst_cs;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        int c = g * 8 + j;
-        d[off_l + c] = to_store<T>(bilerp(cl, C, c, tl));
-        d[off_r + c] = to_store<T>(bilerp(cr, C, c, tr));
-    }
+    float o[8];
+    bilerp8(cl, C, g * 8, tl, o);
+    store8(d + off_l + g * 8, o);
+    bilerp8(cr, C, g * 8, tr, o);
+    store8(d + off_r + g * 8, o);
 }
 
 // a8: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to H x W.
@@ -290,9 +293,12 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
     do { count_launch(); FVV_CHECK_CUDA(cudaGetLastError()); } while (0)
 
 int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float *img0,
-                     float *img1, float *img2, bf16 *img0_b16, cudaStream_t st) {
-    long long n = (long long)n_cams * (Hp / 4) * (Wp / 4);
-    prep_cams_kernel<<<blocks_for(n, 128), 128, 0, st>>>(cams, n_cams, H, W, Hp, Wp, img0, img1, img2, img0_b16);
+                     float *img1, float *img2, cudaStream_t st) {
+    long long n = (long long)n_cams * (Hp / 2) * (Wp / 2);
+    prep_cams_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cams, n_cams, H, W, Hp, Wp, img0, img1);
+    FVV_LAUNCH_CHECK();
+    n = (long long)n_cams * (Hp / 4) * (Wp / 4);
+    box_quarter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(img1, n_cams, Hp / 2, Wp / 2, img2);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
