@@ -119,12 +119,23 @@ __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int o
     }
 }
 
-template <int BN, int CK, int STAGES, int CTAS>
+// MT = 128-pixel row blocks per tile (1 or 2): with MT = 2 each weight slice in
+// shared memory feeds two MMAs (two accumulators), halving weight traffic per FLOP.
+// The accumulators are double-buffered (ACCB = 2) when TMEM has room.
+template <int BN, int MT> struct AccCfg {
+    static constexpr int ACCB = 2 * MT * BN <= 512 ? 2 : 1;
+    static constexpr int COLS_USED = ACCB * MT * BN;
+    static constexpr uint32_t TMEM_COLS =
+        COLS_USED <= 32 ? 32 : (COLS_USED <= 64 ? 64 : (COLS_USED <= 128 ? 128 : (COLS_USED <= 256 ? 256 : 512)));
+};
+
+template <int BN, int CK, int MT, int STAGES, int CTAS>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
-    constexpr uint32_t A_BYTES = 128 * CK * 2, B_BYTES = BN * CK * 2;
+    constexpr uint32_t A_BYTES = 128 * MT * CK * 2, B_BYTES = BN * CK * 2;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
-    constexpr uint32_t TMEM_COLS = (2 * BN) <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+    constexpr int ACCB = AccCfg<BN, MT>::ACCB;
+    constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = ptx::make_idesc(128, BN, 1, 1);
     constexpr int ROW_BYTES = CK * 2;
 
@@ -221,7 +232,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
-                uint32_t d = tmem + acc * BN;
+                uint32_t d = tmem + acc * (MT * BN);
                 bool ok = true;
                 for (int kb = 0; kb < kblocks; ++kb) {
                     if (!wait_bar(ptx::smem_u32(&bars->full[stage]), phase_bit, abort, p.err, 3)) { ok = false; break; }
@@ -229,9 +240,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     uint32_t a0 = ptx::smem_u32(sA + stage * A_STRIDE), b0 = ptx::smem_u32(sB + stage * B_STRIDE);
 #pragma unroll
                     for (int k = 0; k < CK / 16; ++k) {
-                        uint64_t ad = ptx::smem_desc(a0 + k * 32, ROW_BYTES);
                         uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
-                        ptx::mma_bf16(d, ad, bd, IDESC, (kb | k) != 0);
+#pragma unroll
+                        for (int m = 0; m < MT; ++m) {
+                            uint64_t ad = ptx::smem_desc(a0 + m * 128 * ROW_BYTES + k * 32, ROW_BYTES);
+                            ptx::mma_bf16(d + m * BN, ad, bd, IDESC, (kb | k) != 0);
+                        }
                     }
                     issued_any = true;
                     ptx::mma_commit(ptx::smem_u32(&bars->empty[stage]));
@@ -239,7 +253,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 if (!ok) break;
                 ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
-                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+                if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
             }
             if (*abort && issued_any) {
                 // wait (bounded) for the MMAs already issued before TMEM is freed
@@ -261,8 +275,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tile_coords(p, t, ph, n, y0, x0);
             int gy = y0 + dy, gx = x0 + dx;
             bool valid = gy < p.gh && gx < p.gw;
-            uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
-            if (BN == 32 && p.epi.mode == EPI_RESID) {
+            uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
+            if (MT == 1 && BN == 32 && p.epi.mode == EPI_RESID) {
                 // Eq. 2 update of a 4-phase transposed conv with 5 outputs (the VIB
                 // t1 layer): this pixel q of the half grid owns the 4 fine pixels
                 // (2q + phase); their x2 upsampling reads the 3x3 neighbourhood of q
@@ -300,7 +314,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         }
                     }
                 }
-            } else if (BN == 16 && p.epi.mode == EPI_OUTPUT) {
+            } else if (MT == 1 && BN == 16 && p.epi.mode == EPI_OUTPUT) {
                 // residual output fused into the 16 -> 3 conv: I_blend fetched early
                 const bool in_crop = valid && gy < p.epi.crop_h && gx < p.epi.crop_w;
                 size_t pix = ((size_t)n * p.out_h + gy) * p.out_w + gx;
@@ -326,10 +340,17 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             ptx::tc_fence_after();
             const int ncols = p.mode == MODE_T3 ? 4 * p.co : p.co; // columns that hold outputs
 #pragma unroll 1
+            for (int m = 0; m < MT; ++m) {
+            // row block m of the tile: accumulator m, pixel rows m * 128 + lane row
+            const int rm = m * 128 + row;
+            const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
+            const bool valid = gy < p.gh && gx < p.gw;
+            const uint32_t tb = tbase + m * BN;
+#pragma unroll 1
             for (int c = 0; c < BN; c += 16) {
                 uint32_t r[16];
                 __syncwarp();
-                ptx::tmem_ld16(tbase + c, r);
+                ptx::tmem_ld16(tb + c, r);
                 ptx::tmem_ld_wait();
                 if (!valid || c >= ncols) continue;
                 // output pixel and channel of column c (a chunk never straddles a
@@ -371,9 +392,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
             }
+            }
             ptx::tc_fence_before();
             ptx::mbar_arrive(ptx::smem_u32(&bars->tmem_empty[acc]));
-            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
         }
     }
 
@@ -428,25 +450,31 @@ int ck_of(int ci_pad) { return ci_pad >= 64 ? 64 : ci_pad; }
 
 struct Shape { int th_log, tw_log; };
 
-// Tile rectangle with the fewest tiles covering gh x gw (ties: wider).
-Shape pick_shape(int gh, int gw) {
-    Shape best{3, 4};
+// Tile rectangle of 2^pix_log pixels with the fewest tiles covering gh x gw (ties: wider).
+Shape pick_shape(int gh, int gw, int pix_log) {
+    Shape best{pix_log - 4, 4};
     long best_tiles = -1;
-    for (int tw_log = 7; tw_log >= 3; --tw_log) {
-        int th_log = 7 - tw_log;
+    for (int tw_log = pix_log; tw_log >= 3; --tw_log) {
+        int th_log = pix_log - tw_log;
+        if (tw_log > 8 || th_log > 8) continue; // TMA box dimensions are at most 256
         long tiles = (long)ceil_div(gh, 1 << th_log) * ceil_div(gw, 1 << tw_log);
         if (best_tiles < 0 || tiles < best_tiles) { best_tiles = tiles; best = {th_log, tw_log}; }
     }
     return best;
 }
 
-// Resources of one (N tile, channel block) configuration.  Small-N configs put
-// several CTAs on an SM (their TMEM columns and shared memory allow it), so more
-// TMA copies are in flight per SM: those layers are bound by copy latency.
+// Row blocks per tile: two for the wide layers (the weight slice then feeds two MMAs).
+// (N = 256 keeps one block: two 256-column accumulators would fill TMEM and lose the
+// double buffering that hides the epilogue.)
+int mt_for(int bn, int ck) { return ck == 64 && bn == 128 ? 2 : 1; }
+
+// Resources of one (N tile, channel block, row blocks) configuration.  Small-N
+// configs put several CTAs on an SM (their TMEM columns and shared memory allow
+// it), so more TMA copies are in flight per SM: those layers are bound by copy latency.
 constexpr uint32_t kSmemBudget = 220 * 1024; // per SM, for all resident CTAs
-template <int BN, int CK> struct Cfg {
-    static constexpr uint32_t A = ((128 * CK * 2) + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
-    static constexpr uint32_t TMEM_COLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+template <int BN, int CK, int MT> struct Cfg {
+    static constexpr uint32_t A = ((128 * MT * CK * 2) + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
+    static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048) / (A + B)); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for((512 / TMEM_COLS) < 4 ? (512 / TMEM_COLS) : 4);
@@ -459,8 +487,9 @@ int g_num_sms = 0;
 
 template <int BN, int CK>
 int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
-    using C = Cfg<BN, CK>;
-    auto kern = conv_tc_kernel<BN, CK, C::STAGES, C::CTAS>;
+    constexpr int MT = (CK == 64 && BN == 128) ? 2 : 1; // = mt_for(BN, CK)
+    using C = Cfg<BN, CK, MT>;
+    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -577,7 +606,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     else { p.gh = Hin; p.gw = Win; }
     p.out_h = L.kind == K_CONV ? p.gh : 2 * Hin;
     p.out_w = L.kind == K_CONV ? p.gw : 2 * Win;
-    Shape s = pick_shape(p.gh, p.gw);
+    const int mt = mt_for(bn, ck);
+    Shape s = pick_shape(p.gh, p.gw, mt == 2 ? 8 : 7);
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
