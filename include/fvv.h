@@ -130,6 +130,26 @@ int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_flo
 int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int n, int H, int W,
                      void *out, int out_cs, int out_coff, int out_f32, void *stream);
 
+/* One layer of Table 3 with no device allocation at all (the paper has no
+ * counterpart: this exists for callers that may not allocate device memory —
+ * an application that owns a fixed device-memory budget, a real-time loop that
+ * cannot risk the synchronisation an allocation may cause, or a plug-in living in
+ * another framework's memory pool; such callers cannot create an fvv_interp).
+ * Same operation and FP32 arithmetic as fvv_interp_layer on an FP32 handle, but
+ * the weights come from the caller:
+ *   w: DEVICE, the layer's weights in the blob layout (conv [Co][Ci][3][3],
+ *      convT [Ci][Co][4][4]), float32;  b: DEVICE, Co float32 biases;
+ *   in / out: DEVICE float32, as for fvv_interp_layer (zero padding).
+ * The repacked weights live in a fixed device array of 2^20 floats (4 MiB, the
+ * largest layer of Table 3) that every GPU loading the library keeps until exit;
+ * a layer with more weights is rejected with FVV_ESHAPE.  All calls share that
+ * array and it keeps the last call's contents, so calls that overlap on the GPU
+ * (different streams, or another thread) race: serialise them.  The first call on
+ * a device looks up the array's device address (with that device current); make
+ * that first call before any stream capture.  Asynchronous on `stream`. */
+int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in, int in_cs, int in_coff, int n,
+                      int H, int W, float *out, int out_cs, int out_coff, void *stream);
+
 /* Synchronise the device and report whether any bounded device-side wait of
  * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */

@@ -61,6 +61,8 @@ def lib():
         L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
         L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
         L.fvv_interp_status.argtypes = [_P]
+        L.fvv_layer_noalloc.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
         L.fvv_interp_profile.argtypes = [_P, ctypes.c_int]
         L.fvv_interp_layer_stats.argtypes = [_P, _P, _P, _P, ctypes.c_int]
         L.fvv_interp_destroy.argtypes = [_P]
@@ -172,6 +174,13 @@ def fvv_interp_layer(h: int, layer: int, inp, in_cs: int, in_coff: int, n: int, 
                      out, out_cs: int, out_coff: int, out_f32: bool, stream=None):
     _check(lib().fvv_interp_layer(h, layer, _dev(inp), in_cs, in_coff, n, H, W, _dev(out), out_cs, out_coff,
                                   int(out_f32), _stream(stream)))
+
+
+def fvv_layer_noalloc(layer: int, w, b, inp, in_cs: int, in_coff: int, n: int, H: int, W: int,
+                      out, out_cs: int, out_coff: int, stream=None):
+    """One layer with the caller's device weights and no device allocation (see fvv.h)."""
+    _check(lib().fvv_layer_noalloc(layer, _dev(w), _dev(b), _dev(inp), in_cs, in_coff, n, H, W, _dev(out),
+                                   out_cs, out_coff, _stream(stream)))
 
 
 def fvv_interp_status(h: int):
