@@ -59,11 +59,13 @@ typedef struct {
                       midpoint views (t must be k / 2^n) */
     int max_views; /* views per run call the workspace is sized for (>= 1) */
     int max_cams;  /* cameras per batched call (>= 2) */
+    int graphs;    /* 1: each run replays a CUDA graph captured on first use for its
+                      (cameras, views) count; 0: launch kernels directly */
 } fvv_opts;
 
 typedef struct fvv_interp fvv_interp;
 
-/* Default options: FP32, zero padding, direct t, max_views 16, max_cams 2. */
+/* Default options: FP32, zero padding, direct t, max_views 16, max_cams 2, graphs on. */
 void fvv_default_opts(fvv_opts *opts);
 
 /* Create an interpolator for H x W frames.
@@ -154,6 +156,15 @@ int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in
  * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */
 int fvv_interp_status(fvv_interp *h);
+
+/* Tile autotuner: times every candidate tile rectangle (128 or 256 output pixels,
+ * width 8 ... 256) of every tensor-core layer on a forward of n_views views (with
+ * the per-layer events of fvv_interp_profile) and keeps the fastest per layer.
+ * cache_path (may be NULL): a JSON file of earlier results keyed by frame size,
+ * view count and precision; a matching entry is loaded instead of measuring, and
+ * new results are added to the file.  Synchronises the device.  No effect on the
+ * FP32 path (its kernel has no tile choice). */
+int fvv_interp_autotune(fvv_interp *h, int n_views, const char *cache_path);
 
 /* Per-layer timing (the analogue of the paper's per-module latency, Table 2).
  * fvv_interp_profile(h, 1) brackets every convolution launch of later runs with

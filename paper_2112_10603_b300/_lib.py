@@ -34,7 +34,7 @@ class FvvError(RuntimeError):
 
 class fvv_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pad_mode", ctypes.c_int), ("t_mode", ctypes.c_int),
-                ("max_views", ctypes.c_int), ("max_cams", ctypes.c_int)]
+                ("max_views", ctypes.c_int), ("max_cams", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 _lib = None
@@ -61,6 +61,7 @@ def lib():
         L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
         L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
         L.fvv_interp_status.argtypes = [_P]
+        L.fvv_interp_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_char_p]
         L.fvv_layer_noalloc.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
         L.fvv_interp_profile.argtypes = [_P, ctypes.c_int]
@@ -181,6 +182,10 @@ def fvv_layer_noalloc(layer: int, w, b, inp, in_cs: int, in_coff: int, n: int, H
     """One layer with the caller's device weights and no device allocation (see fvv.h)."""
     _check(lib().fvv_layer_noalloc(layer, _dev(w), _dev(b), _dev(inp), in_cs, in_coff, n, H, W, _dev(out),
                                    out_cs, out_coff, _stream(stream)))
+
+
+def fvv_interp_autotune(h: int, n_views: int, cache_path: str | None = None):
+    _check(lib().fvv_interp_autotune(h, n_views, cache_path.encode() if cache_path else None))
 
 
 def fvv_interp_status(h: int):

@@ -110,7 +110,7 @@ __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int o
         if (oy < p.epi.crop_h && ox < p.epi.crop_w) {
             float r = 2.f * sigmoidf_(x) - 1.f;
             float v = fminf(fmaxf(p.epi.ib[pix * 3 + co] + r, 0.f), 1.f);
-            p.epi.final_out[(((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3 + co] = v;
+            (*p.epi.final_out_ref)[(((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3 + co] = v;
         }
     } else if (p.out_f32) {
         ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
@@ -328,7 +328,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 ptx::tmem_ld16(tbase, r);
                 ptx::tmem_ld_wait();
                 if (in_crop) {
-                    float *dst = p.epi.final_out + (((size_t)n * p.epi.crop_h + gy) * p.epi.crop_w + gx) * 3;
+                    float *dst = *p.epi.final_out_ref + (((size_t)n * p.epi.crop_h + gy) * p.epi.crop_w + gx) * 3;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         float z = __uint_as_float(r[k]) + __ldg(p.bias + k);
@@ -606,8 +606,13 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     else { p.gh = Hin; p.gw = Win; }
     p.out_h = L.kind == K_CONV ? p.gh : 2 * Hin;
     p.out_w = L.kind == K_CONV ? p.gw : 2 * Win;
-    const int mt = mt_for(bn, ck);
-    Shape s = pick_shape(p.gh, p.gw, mt == 2 ? 8 : 7);
+    const int mt = mt_for(bn, ck), pix_log = mt == 2 ? 8 : 7;
+    Shape s = pick_shape(p.gh, p.gw, pix_log);
+    const int force = h->tile_force >= 0 ? h->tile_force : h->tile_tw[li]; // autotuned width
+    if (force >= 0) {
+        int tw = force < pix_log ? force : pix_log;
+        if (pix_log - tw <= 8) s = Shape{pix_log - tw, tw};
+    }
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);

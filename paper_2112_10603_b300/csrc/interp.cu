@@ -138,7 +138,7 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
     return launch_conv_simt(a, false, is_bf16(h) && !out_f32, st);
 }
 
-template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st) {
+template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
     const int Hp = h->Hp, Wp = h->Wp, circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
     const bool b16 = is_bf16(h);
     const int cx0 = b16 ? 16 : 7, cx1 = b16 ? 32 : 18, cu0 = b16 ? 16 : 6;
@@ -225,21 +225,21 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, fl
             TcEpi e;
             e.mode = EPI_OUTPUT;
             e.ib = h->ib;
-            e.final_out = out;
+            e.final_out_ref = h->d_outp;
             e.crop_h = h->H;
             e.crop_w = h->W;
             FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st, &e));
         } else {
             FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st));
-            FVV_TRY(launch_output(h->ib, h->z, 3, nv, Hp, Wp, h->H, h->W, out, st));
+            FVV_TRY(launch_output(h->ib, h->z, 3, nv, Hp, Wp, h->H, h->W, h->d_outp, st));
         }
     }
     return FVV_OK;
 }
 
-int interp_forward(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st) {
+int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
     g_launches = 0;
-    int rc = is_bf16(h) ? forward_t<bf16>(h, n_cams, nv, out, st) : forward_t<float>(h, n_cams, nv, out, st);
+    int rc = is_bf16(h) ? forward_t<bf16>(h, n_cams, nv, st) : forward_t<float>(h, n_cams, nv, st);
     h->last_launches = g_launches;
     return rc;
 }
@@ -297,15 +297,17 @@ static int create_impl(fvv_interp *h, const float *blob) {
     FVV_TRY(dalloc_t(h, &h->d_t, V * 4));
     FVV_TRY(dalloc_t(h, &h->d_cams, C * sizeof(float *)));
     FVV_TRY(dalloc_t(h, &h->d_err, 64));
+    FVV_TRY(dalloc_t(h, &h->d_outp, sizeof(float *)));
+    FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, 64));
-    FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + C * sizeof(float *) + 64));
+    FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + (C + 1) * sizeof(float *) + 64));
     FVV_CHECK_CUDA(cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming));
     return FVV_OK;
 }
 
 // Upload the view table and camera pointers through pinned staging.
 static int upload_tables(fvv_interp *h, const float *const *cams, int n_cams, const int *cam_l, const int *cam_r,
-                         const float *t, int nv, cudaStream_t st) {
+                         const float *t, int nv, float *out, cudaStream_t st) {
     FVV_CHECK_CUDA(cudaEventSynchronize(h->stage_done)); // previous upload finished reading the staging
     const int V = h->o.max_views;
     char *s = h->h_stage;
@@ -313,11 +315,45 @@ static int upload_tables(fvv_interp *h, const float *const *cams, int n_cams, co
     memcpy(s + V * 4, cam_r, nv * 4);
     memcpy(s + V * 8, t, nv * 4);
     memcpy(s + V * 12, cams, n_cams * sizeof(float *));
+    char *so = s + V * 12 + h->o.max_cams * sizeof(float *);
+    memcpy(so, &out, sizeof(float *));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_l, s, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_r, s + V * 4, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_t, s + V * 8, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cams, s + V * 12, n_cams * sizeof(float *), cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_outp, so, sizeof(float *), cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaEventRecord(h->stage_done, st));
+    return FVV_OK;
+}
+
+static void drop_graphs(fvv_interp *h) {
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.exec);
+    h->graphs.clear();
+}
+
+// Run the forward for (n_cams, nv) after the tables are uploaded: direct launches
+// while profiling or with graphs off, else replay the graph captured for that count
+// (captured on first use; every buffer it touches is fixed per handle and the
+// per-call data -- view table, camera and output pointers -- is read from device slots).
+static int dispatch_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
+    if (!h->o.graphs || h->profiling) return interp_forward(h, n_cams, nv, st);
+    long long key = (long long)n_cams * 65536 + nv;
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        FVV_CHECK_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+        int rc = interp_forward(h, n_cams, nv, h->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc != FVV_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        FVV_CHECK_CUDA(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        FVV_CHECK_CUDA(e);
+        it = h->graphs.emplace(key, fvv_interp::Graph{exec, h->last_launches}).first;
+    }
+    FVV_CHECK_CUDA(cudaGraphLaunch(it->second.exec, st));
+    h->last_launches = it->second.launches;
     return FVV_OK;
 }
 
@@ -340,6 +376,7 @@ void fvv_default_opts(fvv_opts *o) {
     o->t_mode = FVV_T_DIRECT;
     o->max_views = 16;
     o->max_cams = 2;
+    o->graphs = 1;
 }
 
 const char *fvv_last_error(void) { return g_err.c_str(); }
@@ -369,6 +406,7 @@ int fvv_interp_create(const float *weights, size_t n_floats, int H, int W, const
     }
     fvv_interp *h = new fvv_interp();
     h->H = H; h->W = W; h->o = o;
+    for (int i = 0; i < kNumLayers; ++i) h->tile_tw[i] = -1;
     h->Hp = (H + 15) / 16 * 16; h->Wp = (W + 15) / 16 * 16;
     int rc = create_impl(h, weights);
     if (rc != FVV_OK) { fvv_interp_destroy(h); return rc; }
@@ -387,8 +425,8 @@ int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const f
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<int> cl(n_views, 0), cr(n_views, 1);
     const float *cams[2] = {left, right};
-    FVV_TRY(upload_tables(h, cams, 2, cl.data(), cr.data(), t, n_views, st));
-    return interp_forward(h, 2, n_views, out, st);
+    FVV_TRY(upload_tables(h, cams, 2, cl.data(), cr.data(), t, n_views, out, st));
+    return dispatch_forward(h, 2, n_views, st);
 }
 
 int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
@@ -430,8 +468,8 @@ int fvv_interp_run_batch(fvv_interp *h, const float *const *cams, int n_cams, co
     for (int c = 0; c < n_cams; ++c)
         if (!cams[c]) { set_error("cams[%d] is NULL", c); return FVV_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
-    FVV_TRY(upload_tables(h, cams, n_cams, cl.data(), cr.data(), t, nv, st));
-    return interp_forward(h, n_cams, nv, out, st);
+    FVV_TRY(upload_tables(h, cams, n_cams, cl.data(), cr.data(), t, nv, out, st));
+    return dispatch_forward(h, n_cams, nv, st);
 }
 
 int fvv_interp_peek(fvv_interp *h, int which, int view, float *dst, size_t n_floats) {
@@ -513,6 +551,112 @@ int fvv_interp_layer_stats(fvv_interp *h, double *ms, double *flops, int *launch
     return FVV_OK;
 }
 
+// ---- tile autotuner --------------------------------------------------------
+// Cache file: a JSON object, one entry per line, key "HxW nV pP" -> {layer: log2 width}.
+
+static std::string tune_key(const fvv_interp *h, int nv) {
+    char k[96];
+    snprintf(k, sizeof k, "%dx%d n%d p%d", h->H, h->W, nv, h->o.precision);
+    return k;
+}
+
+static std::map<std::string, std::string> read_tune_cache(const char *path) {
+    std::map<std::string, std::string> m;
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return m;
+    char line[8192];
+    while (fgets(line, sizeof line, f)) {
+        std::string s(line);
+        size_t a = s.find('"'), b = a == std::string::npos ? a : s.find('"', a + 1);
+        size_t lb = s.find('{', b == std::string::npos ? 0 : b), rb = s.rfind('}');
+        if (a == std::string::npos || b == std::string::npos || lb == std::string::npos || rb == std::string::npos ||
+            rb <= lb)
+            continue;
+        m[s.substr(a + 1, b - a - 1)] = s.substr(lb, rb - lb + 1);
+    }
+    fclose(f);
+    return m;
+}
+
+static bool apply_tune_entry(fvv_interp *h, const std::string &obj) {
+    int found = 0;
+    for (int i = 0; i < kNumLayers; ++i) {
+        std::string pat = std::string("\"") + kLayers[i].name + "\":";
+        size_t p = obj.find(pat);
+        if (p == std::string::npos) continue;
+        h->tile_tw[i] = (signed char)atoi(obj.c_str() + p + pat.size());
+        ++found;
+    }
+    return found > 0;
+}
+
+int fvv_interp_autotune(fvv_interp *h, int n_views, const char *cache_path) {
+    clear_error();
+    if (!h) { set_error("NULL handle"); return FVV_EINVAL; }
+    if (n_views < 1 || n_views > h->o.max_views) { set_error("n_views outside [1, max_views]"); return FVV_ESHAPE; }
+    if (!is_bf16(h)) return FVV_OK;
+    const std::string key = tune_key(h, n_views);
+    std::map<std::string, std::string> cache = read_tune_cache(cache_path);
+    drop_graphs(h);
+    if (cache.count(key) && apply_tune_entry(h, cache[key])) return FVV_OK;
+    // frames: zeros (timing does not depend on values)
+    size_t img = (size_t)h->H * h->W * 3;
+    if (!h->d_in) {
+        FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
+        FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
+    }
+    FVV_CHECK_CUDA(cudaMemset(h->d_in, 0, 2 * img * 4));
+    std::vector<float> t(n_views, 0.5f);
+    std::vector<int> cl(n_views, 0), cr(n_views, 1);
+    const float *cams[2] = {h->d_in, h->d_in + img};
+    // -1 = the fewest-tiles default, measured first; a candidate replaces it only if
+    // it is at least 3% faster (timing noise must not flip the choice)
+    const int cands[] = {-1, 3, 4, 5, 6, 7, 8};
+    std::vector<double> best(kNumLayers, 1e30);
+    std::vector<int> pick(kNumLayers, -1);
+    const bool was_profiling = h->profiling;
+    int rc = FVV_OK;
+    for (int c : cands) {
+        h->tile_force = c;
+        std::vector<double> cand_ms(kNumLayers, 1e30);
+        for (int rep = 0; rep < 4 && rc == FVV_OK; ++rep) { // rep 0 warms up
+            if ((rc = fvv_interp_profile(h, 1)) != FVV_OK) break;
+            if ((rc = upload_tables(h, cams, 2, cl.data(), cr.data(), t.data(), n_views, h->d_out, 0)) != FVV_OK) break;
+            if ((rc = interp_forward(h, 2, n_views, 0)) != FVV_OK) break;
+            double ms[kNumLayers];
+            if ((rc = fvv_interp_layer_stats(h, ms, nullptr, nullptr, kNumLayers)) != FVV_OK) break;
+            if (rep == 0) continue;
+            for (int i = 0; i < kNumLayers; ++i)
+                if (ms[i] > 0 && ms[i] < cand_ms[i]) cand_ms[i] = ms[i];
+        }
+        if (rc != FVV_OK) break;
+        for (int i = 0; i < kNumLayers; ++i)
+            if (cand_ms[i] < (c < 0 ? 1e29 : 0.97 * best[i])) { best[i] = cand_ms[i]; pick[i] = c; }
+    }
+    h->tile_force = -1;
+    fvv_interp_profile(h, was_profiling ? 1 : 0);
+    if (rc != FVV_OK) return rc;
+    for (int i = 0; i < kNumLayers; ++i) h->tile_tw[i] = (signed char)pick[i];
+    if (cache_path) {
+        std::string obj = "{";
+        for (int i = 0; i < kNumLayers; ++i) {
+            char e[64];
+            snprintf(e, sizeof e, "%s\"%s\": %d", i ? ", " : "", kLayers[i].name, pick[i]);
+            obj += e;
+        }
+        obj += "}";
+        cache[key] = obj;
+        FILE *f = fopen(cache_path, "w");
+        if (!f) { set_error("cannot write autotune cache %s", cache_path); return FVV_EINVAL; }
+        fprintf(f, "{\n");
+        size_t k = 0;
+        for (auto &kv : cache) fprintf(f, "\"%s\": %s%s\n", kv.first.c_str(), kv.second.c_str(), ++k < cache.size() ? "," : "");
+        fprintf(f, "}\n");
+        fclose(f);
+    }
+    return FVV_OK;
+}
+
 size_t fvv_interp_device_bytes(const fvv_interp *h) { return h ? h->dev_bytes : 0; }
 int fvv_interp_last_launches(const fvv_interp *h) { return h ? h->last_launches : 0; }
 
@@ -524,6 +668,8 @@ void fvv_interp_destroy(fvv_interp *h) {
     if (h->stage_done) cudaEventDestroy(h->stage_done);
     prof_reset(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 

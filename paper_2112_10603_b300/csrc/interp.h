@@ -1,5 +1,6 @@
 // Network executor: layer table, packed weights, workspace and the layer schedule.
 #pragma once
+#include <map>
 #include <vector>
 
 #include "common.h"
@@ -25,7 +26,7 @@ struct TcEpi {
     int mode = EPI_STORE;
     const float *fm_prev = nullptr; // EPI_RESID: previous stage F, M (half grid, 5 ch FP32)
     const float *ib = nullptr;      // EPI_OUTPUT: I_blend on the padded grid (3 ch FP32)
-    float *final_out = nullptr;     // EPI_OUTPUT: cropped n x crop_h x crop_w x 3 output
+    float *const *final_out_ref = nullptr; // EPI_OUTPUT: device slot holding the cropped n x crop_h x crop_w x 3 output
     int crop_h = 0, crop_w = 0;
 };
 
@@ -71,10 +72,20 @@ struct fvv_interp {
     bool profiling = false;
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
+    // output pointer slot read by the last kernel (so a captured graph serves any buffer)
+    float **d_outp = nullptr;
+    // CUDA graphs, one per (cameras, views) count, captured on cap_stream
+    struct Graph { cudaGraphExec_t exec; int launches; };
+    std::map<long long, Graph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    // tile rectangle per layer: log2 of the tile width (-1: fewest-tiles default);
+    // tile_force >= 0 overrides every layer (used while autotuning)
+    signed char tile_tw[fvv::kNumLayers];
+    int tile_force = -1;
 };
 
 namespace fvv {
-int interp_forward(fvv_interp *h, int n_cams, int nv, float *out, cudaStream_t st);
+int interp_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st);
 int dalloc(fvv_interp *h, void **p, size_t bytes);
 int tc_prepare(fvv_interp *h, const float *blob);
 int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,

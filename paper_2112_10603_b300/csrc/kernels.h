@@ -31,7 +31,7 @@ int launch_final_blend(const float *img0, const float *FM, const ViewTab &vt, in
 template <typename T>
 int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, const ViewTab &vt, int nv,
                     int h, int w, int circ, T *dst, int dst_cs, int off_l, int off_r, cudaStream_t st);
-int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *out,
+int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *const *outp,
                   cudaStream_t st);
 
 } // namespace fvv

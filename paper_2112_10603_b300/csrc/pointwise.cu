@@ -270,7 +270,8 @@ __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, con
 
 // a8: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to H x W.
 __global__ void output_kernel(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp,
-                              int H, int W, float *out) {
+                              int H, int W, float *const *outp) {
+    float *out = *outp;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)H * W;
     if (idx >= (long long)nv * P) return;
@@ -346,10 +347,10 @@ int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, i
     return FVV_OK;
 }
 
-int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *out,
+int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *const *outp,
                   cudaStream_t st) {
     long long n = (long long)nv * H * W;
-    output_kernel<<<blocks_for(n, 256), 256, 0, st>>>(ib, z, z_cs, nv, Hp, Wp, H, W, out);
+    output_kernel<<<blocks_for(n, 256), 256, 0, st>>>(ib, z, z_cs, nv, Hp, Wp, H, W, outp);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }

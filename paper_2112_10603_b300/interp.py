@@ -8,10 +8,10 @@ from . import _lib as L
 
 class Interpolator:
     def __init__(self, weights, H: int, W: int, precision: int = L.FVV_FP32, pad_mode: int = L.FVV_PAD_ZERO,
-                 max_views: int = 16, max_cams: int = 2, t_mode: int = L.FVV_T_DIRECT):
+                 max_views: int = 16, max_cams: int = 2, t_mode: int = L.FVV_T_DIRECT, graphs: int = 1):
         self.H, self.W = H, W
         self.opts = L.fvv_default_opts(precision=precision, pad_mode=pad_mode, max_views=max_views,
-                                       max_cams=max_cams, t_mode=t_mode)
+                                       max_cams=max_cams, t_mode=t_mode, graphs=graphs)
         self.h = L.fvv_interp_create(weights, H, W, self.opts)
 
     def run(self, left, right, t, out=None, stream=None):
@@ -37,6 +37,10 @@ class Interpolator:
             out = torch.empty((len(t), self.H, self.W, 3), dtype=torch.float32, device=cams[0].device)
         L.fvv_interp_run_batch(self.h, cams, pair_left, view_offsets, t, out, stream)
         return out
+
+    def autotune(self, n_views: int, cache_path: str | None = None):
+        """Pick each tensor-core layer's tile rectangle by measurement (JSON cache)."""
+        L.fvv_interp_autotune(self.h, n_views, cache_path)
 
     def peek(self, which: str, view: int = 0):
         """Intermediates of the last run: 'vib0'|'vib1'|'vib2'|'blend'|'z' (padded grid)."""
