@@ -190,6 +190,106 @@ def run_rig(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+SERVE_RES = [(720, 1280), (1080, 1920), (2160, 3840)]
+SERVE_MIX = [0.5, 0.4, 0.1]
+
+
+def serve_once(s, fvv, n_users, rate_hz, seconds, seed):
+    """Open-loop load: each user sends viewpoint requests as a Poisson process of
+    rate_hz (uniform pair, t ~ U(0, 1), resolution by SERVE_MIX); a user's previous
+    finished ticket is released when it sends the next.  Returns per-run numbers."""
+    rng = np.random.default_rng(seed)
+    events = []
+    for u in range(n_users):
+        t = rng.exponential(1 / rate_hz)
+        while t < seconds:
+            events.append((t, u))
+            t += rng.exponential(1 / rate_hz)
+    events.sort()
+    outstanding = {}          # user -> tickets not yet released (a running one and a newer one)
+    lat, rejected = [], 0
+
+    def reap(u, wait=False):
+        keep = []
+        for tk in outstanding.get(u, []):
+            while True:
+                try:
+                    st, _, l = fvv.fvv_serve_poll(s, tk)
+                except fvv.FvvError:          # superseded
+                    fvv.fvv_serve_release(s, tk)
+                    break
+                if st == 0:
+                    lat.append(l)
+                    fvv.fvv_serve_release(s, tk)
+                    break
+                if not wait:
+                    keep.append(tk)
+                    break
+                time.sleep(0.0005)
+        outstanding[u] = keep
+
+    t0 = time.perf_counter()
+    base = fvv.fvv_serve_stats_get(s)
+    for when, u in events:
+        while time.perf_counter() - t0 < when:
+            time.sleep(0.0002)
+        reap(u)
+        r = int(rng.choice(3, p=SERVE_MIX))
+        try:
+            outstanding[u].append(fvv.fvv_serve_submit(s, u, int(rng.integers(0, 8)), float(rng.uniform(0, 1)), r))
+        except fvv.FvvError:
+            rejected += 1
+    for u in list(outstanding):               # drain
+        reap(u, wait=True)
+    wall = time.perf_counter() - t0
+    st = fvv.fvv_serve_stats_get(s)
+    done = st["completed"] - base["completed"]
+    sup = st["superseded"] - base["superseded"]
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"users": n_users, "offered_req_per_s": len(events) / seconds, "completed_views_per_s": done / wall,
+            "superseded_frac": sup / max(1, len(events)), "rejected": rejected,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "batches": st["batches"] - base["batches"]}
+
+
+def run_serve(args, rank, world, local):
+    """Multi-user serving: 64 users at 30 Hz each over the 9-camera rig, resolutions
+    50% 1280x720 / 40% 1920x1080 / 10% 3840x2160, continuous batching, latest-wins."""
+    import torch
+    import paper_2112_10603_b300 as fvv
+    from paper_2112_10603_b300 import build as fvv_build
+    from synth import scene, weights
+    fvv_build.build()
+    torch.cuda.set_device(local)
+    n_cams = 9
+    cams = [[torch.from_numpy(c).cuda() for c in scene.rig(5 + r, h, w, n_cams=n_cams, max_disp=MAX_DISP * w / 1920)]
+            for r, (h, w) in enumerate(SERVE_RES)]
+    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=3, res_h=[h for h, _ in SERVE_RES],
+                                    res_w=[w for _, w in SERVE_RES], n_cams=n_cams, slots_per_res=2,
+                                    max_batch=8, pool_views=96, hbm_budget=200 * 2 ** 30)
+    s = fvv.fvv_serve_create(weights.he_init(WEIGHT_SEED), cfg)
+    try:
+        for r in range(3):
+            fvv.fvv_serve_set_frames(s, 0, r, cams[r])
+        serve_once(s, fvv, 16, 30.0, 2.0, 100)       # warm-up: graphs for every batch size
+        main = serve_once(s, fvv, 64, 30.0, args.serve_seconds, 5)
+        sweep = [serve_once(s, fvv, u, 30.0, max(2.0, args.serve_seconds / 3), 50 + u) for u in (4, 8, 16, 32)]
+        st = fvv.fvv_serve_stats_get(s)
+    finally:
+        fvv.fvv_serve_destroy(s)
+    line = {"metric": "served virtual views/s (64 users, mixed resolution)", "value": main["completed_views_per_s"],
+            "unit": "views/s", "n_gpus": world, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic 9-camera rig per resolution, Poisson viewpoint requests",
+            "config": {"workload": "serve: 64 users x 30 Hz, pairs U{0..7}, t ~ U(0,1), res 50/40/10% "
+                                   "720p/1080p/2160p, open loop", "seconds": args.serve_seconds,
+                       "slots_per_res": 2, "max_batch": 8, "hbm_budget_gib": 200},
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "max_ms": main["max_ms"],
+            "offered_req_per_s": main["offered_req_per_s"], "superseded_frac": main["superseded_frac"],
+            "rejected": main["rejected"], "users_sweep": sweep, "device_gib": st["device_bytes"] / 2 ** 30}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def config_dict(args):
     return {"workload": f"1 camera pair 1920x1080 (padded 1920x1088), {len(TS)} views t=k/{len(TS) + 1} per step",
             "H": H, "W": W, "views_per_step": len(TS), "precision": args.precision,
@@ -208,8 +308,10 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--views", type=int, default=7, help="views per step (t = k/(views+1))")
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed steps (for profiling)")
-    ap.add_argument("--workload", default="pair", choices=["pair", "rig"],
-                    help="pair: the headline 1-pair 7-view step; rig: batched 9-camera instants")
+    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve"],
+                    help="pair: the headline 1-pair 7-view step; rig: batched 9-camera instants; "
+                         "serve: 64-user mixed-resolution serving")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     global TS
     TS = [k / (args.views + 1) for k in range(1, args.views + 1)]
@@ -221,6 +323,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "rig":
         return run_rig(args, rank, world, local)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local)
 
     import torch
     import paper_2112_10603_b300 as fvv

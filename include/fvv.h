@@ -178,6 +178,75 @@ int fvv_interp_layer_stats(fvv_interp *h, double *ms, double *flops, int *launch
 
 void fvv_interp_destroy(fvv_interp *h);
 
+/* ------------------------------------------------------------------------
+ * Multi-user server: continuous batching of viewpoint requests.
+ *
+ * The paper's edge media server serves many users from one GPU and organises its
+ * modules around FIFO data channels (Sec. 2, Sec. 3.2, supplement S.1).  Here a
+ * request = (user, camera pair, t, resolution) -> one synthesised view in device
+ * memory.  Per resolution the server holds `slots_per_res` interpolators, each on
+ * its own stream: whenever a slot is free the scheduler thread takes up to
+ * `max_batch` queued requests of that resolution and runs them as one batched
+ * forward, so requests arriving while others run are admitted as slots free up.
+ * A new request from a user replaces that user's request still waiting in the
+ * queue (latest wins; the old ticket polls FVV_ESUPERSEDED).  Admission: every
+ * admitted request holds a view-sized output buffer from a per-resolution pool of
+ * `pool_views` buffers, cut to fit `hbm_budget` (bytes, 0 = no limit) after the
+ * slots' workspaces; an empty pool makes submit return FVV_EBUSY.  The server is
+ * thread-safe.  With fake_ms_per_view > 0 no GPU is used (batches just take
+ * fake_ms_per_view per view on the host): for testing the scheduling logic. */
+
+#define FVV_SERVE_MAX_RES 4
+
+typedef struct {
+    int precision;                  /* FVV_BF16 or FVV_FP32 */
+    int n_res;                      /* resolutions served, 1 .. FVV_SERVE_MAX_RES */
+    int res_h[FVV_SERVE_MAX_RES], res_w[FVV_SERVE_MAX_RES];
+    int n_cams;                     /* cameras of the rig; pair p = cameras p, p + 1 */
+    int slots_per_res;              /* concurrent batches per resolution */
+    int max_batch;                  /* views per batch */
+    int pool_views;                 /* output buffers per resolution (before the budget cut) */
+    size_t hbm_budget;              /* device bytes the server may hold; 0 = unlimited */
+    double fake_ms_per_view;        /* > 0: no GPU, simulated batches (tests) */
+} fvv_serve_cfg;
+
+typedef struct {
+    long long submitted, completed, superseded, rejected, failed, batches, batched_views, queued;
+    double p50_ms, p99_ms, max_ms;  /* latency submit -> view ready, completed requests */
+    size_t device_bytes;
+} fvv_serve_stats;
+
+typedef struct fvv_server fvv_server;
+
+/* Defaults: BF16, one resolution 1080 x 1920, 9 cameras, 2 slots, batches of 8,
+ * 64 pooled output views, no budget limit, real GPU. */
+void fvv_serve_default_cfg(fvv_serve_cfg *cfg);
+
+/* weights: as for fvv_interp_create (may be NULL with fake_ms_per_view > 0). */
+int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg *cfg, fvv_server **out);
+
+/* Frames of capture instant `instant` at resolution res_id: n_cams DEVICE pointers
+ * (H x W x 3 float32, caller-owned, kept valid until replaced).  Batches use the
+ * frames set last; a slot reuses its pyramid and ContextNet features while the
+ * instant is unchanged. */
+int fvv_serve_set_frames(fvv_server *s, int64_t instant, int res_id, const float *const *cams_dev);
+
+/* Queue a request; *ticket identifies it.  FVV_EBUSY when the output pool is full. */
+int fvv_serve_submit(fvv_server *s, int user, int pair, float t, int res_id, uint64_t *ticket);
+
+/* 0 = done (*out_dev: the view, H x W x 3 float32 DEVICE, valid until release;
+ * *latency_ms: submit -> ready), 1 = pending, FVV_ESUPERSEDED, FVV_ENOTFOUND, or
+ * FVV_ECUDA if its batch failed. */
+int fvv_serve_poll(fvv_server *s, uint64_t ticket, const float **out_dev, double *latency_ms);
+
+/* Forget a finished ticket and return its output buffer to the pool (1 if still pending). */
+int fvv_serve_release(fvv_server *s, uint64_t ticket);
+
+int fvv_serve_stats_get(fvv_server *s, fvv_serve_stats *out);
+
+/* Stops the scheduler, waits for batches on the device, frees everything. */
+void fvv_serve_destroy(fvv_server *s);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *fvv_last_error(void);
 

@@ -214,3 +214,100 @@ def fvv_interp_destroy(h: int):
 
 def fvv_last_error() -> str:
     return lib().fvv_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# server
+
+FVV_SERVE_MAX_RES = 4
+
+
+class fvv_serve_cfg(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("n_res", ctypes.c_int),
+                ("res_h", ctypes.c_int * FVV_SERVE_MAX_RES), ("res_w", ctypes.c_int * FVV_SERVE_MAX_RES),
+                ("n_cams", ctypes.c_int), ("slots_per_res", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("pool_views", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("fake_ms_per_view", ctypes.c_double)]
+
+
+class fvv_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in ("submitted", "completed", "superseded", "rejected", "failed",
+                                                   "batches", "batched_views", "queued")] + \
+               [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+def _serve_sigs(L):
+    if getattr(L, "_serve_ready", False):
+        return L
+    L.fvv_serve_default_cfg.argtypes = [ctypes.POINTER(fvv_serve_cfg)]
+    L.fvv_serve_create.argtypes = [_P, ctypes.c_size_t, ctypes.POINTER(fvv_serve_cfg), ctypes.POINTER(_P)]
+    L.fvv_serve_set_frames.argtypes = [_P, ctypes.c_int64, ctypes.c_int, _P]
+    L.fvv_serve_submit.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    L.fvv_serve_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double)]
+    L.fvv_serve_release.argtypes = [_P, ctypes.c_uint64]
+    L.fvv_serve_stats_get.argtypes = [_P, ctypes.POINTER(fvv_serve_stats)]
+    L.fvv_serve_destroy.argtypes = [_P]
+    L._serve_ready = True
+    return L
+
+
+def fvv_serve_default_cfg(**kw) -> fvv_serve_cfg:
+    c = fvv_serve_cfg()
+    _serve_sigs(lib()).fvv_serve_default_cfg(ctypes.byref(c))
+    for k, v in kw.items():
+        if k in ("res_h", "res_w"):
+            for i, x in enumerate(v):
+                getattr(c, k)[i] = int(x)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def fvv_serve_create(weights, cfg: fvv_serve_cfg) -> int:
+    L = _serve_sigs(lib())
+    if weights is None:
+        wp, n = None, 0
+    else:
+        w, wp = _host_f32(weights)
+        n = w.size
+    s = _P()
+    _check(L.fvv_serve_create(wp, n, ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def fvv_serve_set_frames(s: int, instant: int, res_id: int, cams):
+    ptrs = (ctypes.c_void_p * len(cams))(*[_dev(c) for c in cams])
+    _check(_serve_sigs(lib()).fvv_serve_set_frames(s, instant, res_id, ptrs))
+
+
+def fvv_serve_submit(s: int, user: int, pair: int, t: float, res_id: int) -> int:
+    tk = ctypes.c_uint64()
+    _check(_serve_sigs(lib()).fvv_serve_submit(s, user, pair, float(t), res_id, ctypes.byref(tk)))
+    return tk.value
+
+
+def fvv_serve_poll(s: int, ticket: int):
+    """(state, device pointer, latency_ms): state 0 done, 1 pending; raises on errors."""
+    p, lat = ctypes.c_void_p(), ctypes.c_double()
+    rc = _serve_sigs(lib()).fvv_serve_poll(s, ticket, ctypes.byref(p), ctypes.byref(lat))
+    if rc < 0:
+        raise FvvError(rc, lib().fvv_last_error().decode())
+    return rc, p.value, lat.value
+
+
+def fvv_serve_release(s: int, ticket: int) -> int:
+    rc = _serve_sigs(lib()).fvv_serve_release(s, ticket)
+    if rc < 0:
+        raise FvvError(rc, lib().fvv_last_error().decode())
+    return rc
+
+
+def fvv_serve_stats_get(s: int) -> dict:
+    st = fvv_serve_stats()
+    _check(_serve_sigs(lib()).fvv_serve_stats_get(s, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in fvv_serve_stats._fields_}
+
+
+def fvv_serve_destroy(s: int):
+    _serve_sigs(lib()).fvv_serve_destroy(s)

@@ -147,10 +147,10 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     T *U[5];
     for (int k = 0; k < 5; ++k) U[k] = (T *)h->u[k];
 
-    // a0: pyramid of every camera
-    FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
-    // a1: ContextNet, batched over cameras
-    {
+    // a0: pyramid of every camera; a1: ContextNet, batched over cameras.  Skipped
+    // when the caller (the server) knows the frames are those of the handle's last run.
+    if (!h->skip_cams) FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
+    if (!h->skip_cams) {
         int hh = Hp, ww = Wp;
         const void *cur = h->img0; // FP32 frame: the 3-channel first layer runs on the SIMT kernel
         int cur_cs = 3;
@@ -337,7 +337,7 @@ static void drop_graphs(fvv_interp *h) {
 // per-call data -- view table, camera and output pointers -- is read from device slots).
 static int dispatch_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
     if (!h->o.graphs || h->profiling) return interp_forward(h, n_cams, nv, st);
-    long long key = (long long)n_cams * 65536 + nv;
+    long long key = ((long long)n_cams * 65536 + nv) * 2 + (h->skip_cams ? 1 : 0);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;

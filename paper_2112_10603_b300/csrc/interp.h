@@ -82,6 +82,9 @@ struct fvv_interp {
     // tile_force >= 0 overrides every layer (used while autotuning)
     signed char tile_tw[fvv::kNumLayers];
     int tile_force = -1;
+    // set by the server while the frames (and so the pyramid and ContextNet features
+    // already in this handle's workspace) are those of its previous run
+    int skip_cams = 0;
 };
 
 namespace fvv {

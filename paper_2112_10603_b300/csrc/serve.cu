@@ -1,0 +1,413 @@
+// Multi-user view-interpolation server (fvv_serve_*): continuous batching of
+// viewpoint requests of mixed resolution on one GPU.
+//
+// The paper's edge server decouples its load from the number of users by
+// rendering dense views once per instant and streaming them (Sec. 3.2); it
+// organises its modules around FIFO data channels with PUT/GET (supplement S.1,
+// "4U" model).  This server keeps that structure — a request channel in, a
+// completion channel out — around the VINet forward:
+//  * per resolution, `slots` interpolator handles, each with its own CUDA stream,
+//    so a batch can start while others are still on the device;
+//  * a scheduler thread takes up to max_batch queued requests of one resolution
+//    whenever one of its slots is free (requests that arrive meanwhile simply wait
+//    for the next free slot: continuous batching), groups them by camera pair and
+//    runs them as ONE batched forward (fvv_interp_run_batch: one graph launch);
+//  * latest-wins per user: a new request from a user replaces that user's request
+//    still waiting in the queue (the old ticket then polls FVV_ESUPERSEDED);
+//  * admission by HBM budget: every admitted request holds one view-sized output
+//    buffer from a pool sized from the budget left after the slots' workspaces;
+//    when the pool is empty, submit returns FVV_EBUSY;
+//  * a slot remembers which frame instant its pyramid/ContextNet features belong
+//    to and skips recomputing them for the next batch of the same instant;
+//  * completion is signalled by a host callback on the slot stream, which stamps
+//    the latency (submit -> views in their output buffers).
+// With cfg.fake_ms_per_view > 0 nothing touches the GPU: a batch "runs" for
+// fake_ms_per_view x views milliseconds on the scheduler thread, so the queueing,
+// supersession, admission and latency logic can be tested on any machine.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "interp.h"
+
+namespace fvv {
+namespace {
+
+enum { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_SUPERSEDED = 3, RQ_FAILED = 4 };
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    int user = 0, pair = 0, res = 0, state = RQ_QUEUED, buf = -1;
+    float t = 0.f;
+    double t_submit = 0, t_done = 0;
+};
+
+struct Batch;
+
+struct Slot {
+    fvv_interp *h = nullptr;
+    cudaStream_t st = nullptr;
+    float *out = nullptr;       // max_batch views
+    bool busy = false;
+    long long frames_id = -1;   // instant whose features are in the workspace
+};
+
+struct Res {
+    int H = 0, W = 0;
+    std::vector<Slot> slots;
+    std::vector<float *> pool; // view-sized output buffers
+    std::vector<int> free_bufs;
+    std::deque<uint64_t> queue;
+    std::vector<const float *> cams;
+    long long frames_id = -1;
+};
+
+} // namespace
+} // namespace fvv
+
+using namespace fvv;
+
+struct fvv_server {
+    fvv_serve_cfg cfg{};
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread sched;
+    bool stop = false;
+    std::vector<Res> res;
+    std::unordered_map<uint64_t, Request> reqs;
+    std::unordered_map<int, uint64_t> queued_of_user; // user -> ticket still queued
+    uint64_t next_ticket = 1;
+    fvv_serve_stats st{};
+    std::vector<double> lat; // completed latencies (ms)
+    size_t dev_bytes = 0;
+};
+
+namespace fvv {
+namespace {
+
+struct Batch {
+    fvv_server *s;
+    int res, slot;
+    std::vector<uint64_t> tickets;
+};
+
+void finish_batch(Batch *b, bool ok) {
+    fvv_server *s = b->s;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        double t = now_ms();
+        for (uint64_t tk : b->tickets) {
+            auto it = s->reqs.find(tk);
+            if (it == s->reqs.end()) continue;
+            Request &r = it->second;
+            r.state = ok ? RQ_DONE : RQ_FAILED;
+            r.t_done = t;
+            if (ok) {
+                s->st.completed++;
+                s->lat.push_back(t - r.t_submit);
+            } else {
+                s->st.failed++;
+            }
+        }
+        s->st.batches++;
+        s->st.batched_views += b->tickets.size();
+        s->res[b->res].slots[b->slot].busy = false;
+    }
+    s->cv.notify_all();
+    delete b;
+}
+
+void CUDART_CB batch_done_cb(void *p) { finish_batch(static_cast<Batch *>(p), true); }
+
+// Launch one batch on a free slot (called without the lock held).
+int launch_batch(fvv_server *s, Batch *b, const std::vector<Request> &rq, const std::vector<const float *> &cams,
+                 long long frames_id) {
+    Res &R = s->res[b->res];
+    Slot &sl = R.slots[b->slot];
+    const int n = (int)rq.size();
+    if (s->cfg.fake_ms_per_view > 0) {
+        std::this_thread::sleep_for(std::chrono::microseconds((long long)(1000.0 * s->cfg.fake_ms_per_view * n)));
+        finish_batch(b, true);
+        return FVV_OK;
+    }
+    // group by pair: rq is sorted by pair already
+    std::vector<int> pair_left, offs{0};
+    std::vector<float> t(n);
+    for (int i = 0; i < n; ++i) {
+        if (pair_left.empty() || pair_left.back() != rq[i].pair) {
+            if (!pair_left.empty()) offs.push_back(i);
+            pair_left.push_back(rq[i].pair);
+        }
+        t[i] = rq[i].t;
+    }
+    offs.push_back(n);
+    sl.h->skip_cams = sl.frames_id == frames_id ? 1 : 0;
+    int rc = fvv_interp_run_batch(sl.h, cams.data(), (int)cams.size(), pair_left.data(), offs.data(), t.data(),
+                                  (int)pair_left.size(), sl.out, sl.st);
+    sl.h->skip_cams = 0;
+    if (rc == FVV_OK) {
+        sl.frames_id = frames_id;
+        const size_t view = (size_t)R.H * R.W * 3;
+        for (int i = 0; i < n && rc == FVV_OK; ++i)
+            if (cudaMemcpyAsync(R.pool[rq[i].buf], sl.out + i * view, view * 4, cudaMemcpyDeviceToDevice, sl.st) !=
+                cudaSuccess)
+                rc = FVV_ECUDA;
+    }
+    if (rc == FVV_OK && cudaLaunchHostFunc(sl.st, batch_done_cb, b) != cudaSuccess) rc = FVV_ECUDA;
+    if (rc != FVV_OK) {
+        sl.frames_id = -1;
+        finish_batch(b, false);
+    }
+    return rc;
+}
+
+void scheduler(fvv_server *s) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool launched = false;
+        for (int r = 0; r < (int)s->res.size() && !s->stop; ++r) {
+            Res &R = s->res[r];
+            int free_slot = -1;
+            for (int k = 0; k < (int)R.slots.size(); ++k)
+                if (!R.slots[k].busy) { free_slot = k; break; }
+            if (free_slot < 0 || R.queue.empty() || R.cams.empty()) continue;
+            // take up to max_batch requests, oldest first
+            Batch *b = new Batch{s, r, free_slot, {}};
+            std::vector<Request> rq;
+            while (!R.queue.empty() && (int)b->tickets.size() < s->cfg.max_batch) {
+                uint64_t tk = R.queue.front();
+                R.queue.pop_front();
+                auto it = s->reqs.find(tk);
+                if (it == s->reqs.end() || it->second.state != RQ_QUEUED) continue;
+                it->second.state = RQ_RUNNING;
+                auto q = s->queued_of_user.find(it->second.user);
+                if (q != s->queued_of_user.end() && q->second == tk) s->queued_of_user.erase(q);
+                b->tickets.push_back(tk);
+            }
+            if (b->tickets.empty()) { delete b; continue; }
+            std::sort(b->tickets.begin(), b->tickets.end(),
+                      [&](uint64_t a, uint64_t c) { return s->reqs[a].pair < s->reqs[c].pair; });
+            for (uint64_t tk : b->tickets) rq.push_back(s->reqs[tk]);
+            R.slots[free_slot].busy = true;
+            std::vector<const float *> cams = R.cams;
+            long long fid = R.frames_id;
+            lk.unlock();
+            launch_batch(s, b, rq, cams, fid);
+            lk.lock();
+            launched = true;
+        }
+        if (!launched) s->cv.wait_for(lk, std::chrono::milliseconds(2));
+    }
+}
+
+} // namespace
+} // namespace fvv
+
+extern "C" {
+
+void fvv_serve_default_cfg(fvv_serve_cfg *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->precision = FVV_BF16;
+    c->n_res = 1;
+    c->res_h[0] = 1080;
+    c->res_w[0] = 1920;
+    c->n_cams = 9;
+    c->slots_per_res = 2;
+    c->max_batch = 8;
+    c->hbm_budget = 0;
+    c->pool_views = 64;
+    c->fake_ms_per_view = 0.0;
+}
+
+int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg *cfg, fvv_server **out) {
+    clear_error();
+    if (!cfg || !out || (!weights && cfg->fake_ms_per_view <= 0)) { set_error("NULL argument"); return FVV_EINVAL; }
+    *out = nullptr;
+    if (cfg->n_res < 1 || cfg->n_res > FVV_SERVE_MAX_RES || cfg->slots_per_res < 1 || cfg->max_batch < 1 ||
+        cfg->n_cams < 2 || cfg->pool_views < 1) {
+        set_error("bad server configuration"); return FVV_EINVAL;
+    }
+    fvv_server *s = new fvv_server();
+    s->cfg = *cfg;
+    s->res.resize(cfg->n_res);
+    int rc = FVV_OK;
+    for (int r = 0; r < cfg->n_res && rc == FVV_OK; ++r) {
+        Res &R = s->res[r];
+        R.H = cfg->res_h[r];
+        R.W = cfg->res_w[r];
+        R.slots.resize(cfg->slots_per_res);
+        if (cfg->fake_ms_per_view > 0) {
+            R.pool.assign(cfg->pool_views, nullptr);
+        } else {
+            fvv_opts o;
+            fvv_default_opts(&o);
+            o.precision = cfg->precision;
+            o.max_views = cfg->max_batch;
+            o.max_cams = cfg->n_cams;
+            for (auto &sl : R.slots) {
+                if ((rc = fvv_interp_create(weights, n_floats, R.H, R.W, &o, &sl.h)) != FVV_OK) break;
+                if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaMalloc(&sl.out, (size_t)cfg->max_batch * R.H * R.W * 3 * 4) != cudaSuccess) {
+                    set_error("server: slot allocation failed"); rc = FVV_ENOMEM; break;
+                }
+                s->dev_bytes += fvv_interp_device_bytes(sl.h) + (size_t)cfg->max_batch * R.H * R.W * 12;
+            }
+        }
+    }
+    // output pool: pool_views per resolution, cut to what the HBM budget leaves
+    for (int r = 0; r < cfg->n_res && rc == FVV_OK && cfg->fake_ms_per_view <= 0; ++r) {
+        Res &R = s->res[r];
+        size_t view = (size_t)R.H * R.W * 12;
+        int n = cfg->pool_views;
+        if (cfg->hbm_budget > 0) {
+            size_t left = cfg->hbm_budget > s->dev_bytes ? cfg->hbm_budget - s->dev_bytes : 0;
+            size_t per_res = left / (size_t)(cfg->n_res - r);
+            n = (int)std::min<size_t>((size_t)n, per_res / view);
+        }
+        if (n < 1) { set_error("HBM budget leaves no output buffer at %dx%d", R.H, R.W); rc = FVV_EBUSY; break; }
+        R.pool.assign(n, nullptr);
+        for (auto &p : R.pool)
+            if (cudaMalloc(&p, view) != cudaSuccess) { set_error("server: pool allocation failed"); rc = FVV_ENOMEM; break; }
+        s->dev_bytes += (size_t)n * view;
+    }
+    if (rc != FVV_OK) { fvv_serve_destroy(s); return rc; }
+    for (auto &R : s->res)
+        for (int i = (int)R.pool.size() - 1; i >= 0; --i) R.free_bufs.push_back(i);
+    s->sched = std::thread(scheduler, s);
+    *out = s;
+    return FVV_OK;
+}
+
+int fvv_serve_set_frames(fvv_server *s, int64_t instant, int res_id, const float *const *cams_dev) {
+    clear_error();
+    if (!s || !cams_dev || res_id < 0 || res_id >= (int)s->res.size()) { set_error("bad arguments"); return FVV_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    Res &R = s->res[res_id];
+    R.cams.assign(cams_dev, cams_dev + s->cfg.n_cams);
+    R.frames_id = instant;
+    s->cv.notify_all();
+    return FVV_OK;
+}
+
+int fvv_serve_submit(fvv_server *s, int user, int pair, float t, int res_id, uint64_t *ticket) {
+    clear_error();
+    if (!s || !ticket || res_id < 0 || res_id >= (int)s->res.size() || pair < 0 || pair + 1 >= s->cfg.n_cams ||
+        !(t >= 0.f && t <= 1.f)) {
+        set_error("bad request"); return FVV_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    Res &R = s->res[res_id];
+    s->st.submitted++;
+    // latest wins: the user's request still waiting is replaced (its buffer reused)
+    int buf = -1;
+    auto q = s->queued_of_user.find(user);
+    if (q != s->queued_of_user.end()) {
+        Request &old = s->reqs[q->second];
+        if (old.state == RQ_QUEUED) {
+            old.state = RQ_SUPERSEDED;
+            old.t_done = now_ms();
+            s->st.superseded++;
+            if (old.res == res_id) buf = old.buf;
+            else s->res[old.res].free_bufs.push_back(old.buf);
+            old.buf = -1;
+        }
+        s->queued_of_user.erase(q);
+    }
+    if (buf < 0) {
+        if (R.free_bufs.empty()) { s->st.rejected++; set_error("admission refused: output pool (HBM budget) full"); return FVV_EBUSY; }
+        buf = R.free_bufs.back();
+        R.free_bufs.pop_back();
+    }
+    uint64_t tk = s->next_ticket++;
+    Request r;
+    r.user = user; r.pair = pair; r.res = res_id; r.t = t; r.buf = buf; r.t_submit = now_ms();
+    s->reqs[tk] = r;
+    R.queue.push_back(tk);
+    s->queued_of_user[user] = tk;
+    *ticket = tk;
+    s->cv.notify_all();
+    return FVV_OK;
+}
+
+int fvv_serve_poll(fvv_server *s, uint64_t ticket, const float **out_dev, double *latency_ms) {
+    clear_error();
+    if (!s) { set_error("NULL server"); return FVV_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("unknown ticket"); return FVV_ENOTFOUND; }
+    Request &r = it->second;
+    switch (r.state) {
+    case RQ_DONE:
+        if (out_dev) *out_dev = r.buf >= 0 ? s->res[r.res].pool[r.buf] : nullptr;
+        if (latency_ms) *latency_ms = r.t_done - r.t_submit;
+        return 0;
+    case RQ_SUPERSEDED: set_error("superseded by a newer request of the same user"); return FVV_ESUPERSEDED;
+    case RQ_FAILED: set_error("the batch holding this request failed"); return FVV_ECUDA;
+    default: return 1;
+    }
+}
+
+int fvv_serve_release(fvv_server *s, uint64_t ticket) {
+    clear_error();
+    if (!s) { set_error("NULL server"); return FVV_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("unknown ticket"); return FVV_ENOTFOUND; }
+    Request &r = it->second;
+    if (r.state == RQ_QUEUED || r.state == RQ_RUNNING) { set_error("request still pending"); return 1; }
+    if (r.buf >= 0) s->res[r.res].free_bufs.push_back(r.buf);
+    s->reqs.erase(it);
+    return FVV_OK;
+}
+
+int fvv_serve_stats_get(fvv_server *s, fvv_serve_stats *out) {
+    clear_error();
+    if (!s || !out) { set_error("NULL argument"); return FVV_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->st;
+    std::vector<double> l = s->lat;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double q) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(q * (l.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = l.empty() ? 0.0 : l.back();
+    out->device_bytes = s->dev_bytes;
+    out->queued = 0;
+    for (auto &R : s->res) out->queued += (long long)R.queue.size();
+    return FVV_OK;
+}
+
+void fvv_serve_destroy(fvv_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->sched.joinable()) s->sched.join();
+    if (s->cfg.fake_ms_per_view <= 0) {
+        for (auto &R : s->res) {
+            for (auto &sl : R.slots) {
+                if (sl.st) cudaStreamSynchronize(sl.st); // host callbacks of in-flight batches run first
+                if (sl.st) cudaStreamDestroy(sl.st);
+                if (sl.out) cudaFree(sl.out);
+                fvv_interp_destroy(sl.h);
+            }
+            for (float *p : R.pool) if (p) cudaFree(p);
+        }
+    }
+    delete s;
+}
+
+} // extern "C"

@@ -1,0 +1,66 @@
+"""The server on the GPU: every result of a mixed-resolution, mixed-pair request mix
+equals the same view computed alone by an interpolator (bit for bit: the batch is
+one forward over independent views, and each output element's arithmetic does not
+depend on its neighbours in the batch)."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import paper_2112_10603_b300 as fvv
+from synth import scene
+from tests.gpu_common import blob
+
+pytestmark = pytest.mark.gpu
+
+
+def _fetch(ptr, shape):
+    """Host copy of a device buffer the server owns (test helper)."""
+    out = np.empty(shape, np.float32)
+    rt = ctypes.CDLL("libcudart.so.13")
+    rc = rt.cudaMemcpy(ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(ptr), ctypes.c_size_t(out.nbytes), 2)
+    assert rc == 0
+    return out
+
+
+def test_server_mix_matches_alone():
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    sizes = [(48, 80), (64, 96)]
+    cams = {r: [torch.from_numpy(c).cuda() for c in scene.rig(20 + r, h, w, n_cams=3, max_disp=6.0)]
+            for r, (h, w) in enumerate(sizes)}
+    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=2, res_h=[h for h, _ in sizes],
+                                    res_w=[w for _, w in sizes], n_cams=3, slots_per_res=2, max_batch=3,
+                                    pool_views=16)
+    s = fvv.fvv_serve_create(blob(), cfg)
+    try:
+        for r in range(2):
+            fvv.fvv_serve_set_frames(s, 0, r, cams[r])
+        rng = np.random.default_rng(3)
+        reqs = []
+        for u in range(10):
+            r, p, t = int(rng.integers(0, 2)), int(rng.integers(0, 2)), float(rng.uniform(0, 1))
+            reqs.append((fvv.fvv_serve_submit(s, u, p, t, r), r, p, t))
+            time.sleep(0.002 * (u % 3))          # arrivals spread over several batches
+        alone = {r: fvv.Interpolator(blob(), h, w, precision=fvv.FVV_BF16, max_views=1)
+                 for r, (h, w) in enumerate(sizes)}
+        for tk, r, p, t in reqs:
+            t0 = time.time()
+            while True:
+                st, ptr, lat = fvv.fvv_serve_poll(s, tk)
+                if st == 0:
+                    break
+                assert time.time() - t0 < 30
+                time.sleep(0.001)
+            h, w = sizes[r]
+            got = _fetch(ptr, (h, w, 3))
+            ref = alone[r].run(cams[r][p], cams[r][p + 1], [t]).cpu().numpy()[0]
+            np.testing.assert_array_equal(got, ref)
+            assert lat > 0
+            assert fvv.fvv_serve_release(s, tk) == 0
+        st = fvv.fvv_serve_stats_get(s)
+        assert st["completed"] == 10 and st["failed"] == 0 and st["device_bytes"] > 0
+    finally:
+        fvv.fvv_serve_destroy(s)
