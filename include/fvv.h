@@ -157,6 +157,22 @@ int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */
 int fvv_interp_status(fvv_interp *h);
 
+/* FP8 calibration (FVV_FP8 handles only; required before their first run).
+ * On FP8 handles the six 256 -> 256 convs of every VIBlock (72% of the FLOPs,
+ * Table 3) run with E4M3 operands and FP32 accumulation: weights carry one scale
+ * per output channel, s_w = max |w| / 448, fixed at create; each such conv's input
+ * carries one scale per tensor, s_a = (max |input| over the calibration views) /
+ * 448, measured here by running the network in BF16 on n_pairs frame pairs at
+ * t = 0.25, 0.5, 0.75.  The producing layer writes E4M3 codes of value / s_a
+ * (round to nearest even, saturating); the epilogue dequantises by s_a * s_w[co].
+ * frames: DEVICE, n_pairs x 2 x H x W x 3 float32 (left, right of each pair).
+ * Synchronises `stream`.  Every other layer and all sampling stay as on FVV_BF16. */
+int fvv_calibrate_fp8(fvv_interp *h, const float *frames, int n_pairs, void *stream);
+
+/* Scales of an FP8 layer after calibration: *s_a (input, per tensor) and the first
+ * n per-output-channel weight scales s_w.  For tests and inspection. */
+int fvv_interp_fp8_scales(fvv_interp *h, int layer, float *s_a, float *s_w, int n);
+
 /* Tile autotuner: times every candidate tile rectangle (128 or 256 output pixels,
  * width 8 ... 256) of every tensor-core layer on a forward of n_views views (with
  * the per-layer events of fvv_interp_profile) and keeps the fastest per layer.

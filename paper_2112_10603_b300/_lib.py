@@ -311,3 +311,20 @@ def fvv_serve_stats_get(s: int) -> dict:
 
 def fvv_serve_destroy(s: int):
     _serve_sigs(lib()).fvv_serve_destroy(s)
+
+
+def fvv_calibrate_fp8(h: int, frames, n_pairs: int, stream=None):
+    """frames: CUDA float32 tensor n_pairs x 2 x H x W x 3 (left, right of each pair)."""
+    L = lib()
+    L.fvv_calibrate_fp8.argtypes = [_P, _P, ctypes.c_int, _P]
+    _check(L.fvv_calibrate_fp8(h, _dev(frames), n_pairs, _stream(stream)))
+
+
+def fvv_interp_fp8_scales(h: int, layer: int, n: int):
+    """(s_a, s_w[:n]) of an FP8 layer after calibration."""
+    L = lib()
+    L.fvv_interp_fp8_scales.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int]
+    sa = ctypes.c_float()
+    sw = np.zeros(n, np.float32)
+    _check(L.fvv_interp_fp8_scales(h, layer, ctypes.byref(sa), sw.ctypes.data, n))
+    return sa.value, sw

@@ -21,6 +21,7 @@
 // global memory, tells the other roles to stop, drains and frees TMEM, returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <cstring>
 #include <vector>
@@ -55,7 +56,16 @@ struct TcParams {
     const float *bias;
     int *err;
     TcEpi epi;
+    // FP8 (E4M3) operands: the accumulator is in units of s_a * s_w[co]
+    const float *acc_scale; // per output channel, NULL for BF16 operands
+    int out_fp8;            // store E4M3 codes of value * out_q (saturating)
+    float out_q;
+    float *amax;            // calibration: running max |output| (NULL: off)
 };
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
 
 struct __align__(8) Bars {
     uint64_t full[8], empty[8], tmem_full[2], tmem_empty[2], drain;
@@ -95,8 +105,9 @@ __device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase
 // One output element of the epilogue (scalar path): bias, ReLU, then store, or
 // the fused Eq. 2 update, or the fused residual output.
 __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int ox, int co, float acc) {
-    float x = acc + __ldg(p.bias + co);
+    float x = acc * (p.acc_scale ? __ldg(p.acc_scale + co) : 1.f) + __ldg(p.bias + co);
     if (p.relu) x = fmaxf(x, 0.f);
+    if (p.amax) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(fabsf(x)));
     size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
     if (p.epi.mode == EPI_RESID) {
         // F^s, M^s = up(F^{s-1}) x 2, up(M^{s-1}) + Res^s; previous stage on the half grid
@@ -114,6 +125,8 @@ __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int o
         }
     } else if (p.out_f32) {
         ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
+    } else if (p.out_fp8) {
+        ((uint8_t *)p.out)[pix * p.out_cs + p.out_coff + co] = to_e4m3(x * p.out_q);
     } else {
         ((bf16 *)p.out)[pix * p.out_cs + p.out_coff + co] = __float2bfloat16_rn(x);
     }
@@ -129,15 +142,18 @@ template <int BN, int MT> struct AccCfg {
         COLS_USED <= 32 ? 32 : (COLS_USED <= 64 ? 64 : (COLS_USED <= 128 ? 128 : (COLS_USED <= 256 ? 256 : 512)));
 };
 
-template <int BN, int CK, int MT, int STAGES, int CTAS>
+// F8 = 1: E4M3 operands (kind::f8f6f4, K = 32 per MMA), else BF16 (kind::f16, K = 16);
+// either way one MMA consumes 32 bytes of every operand row.
+template <int BN, int CK, int MT, int STAGES, int CTAS, int F8>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
-    constexpr uint32_t A_BYTES = 128 * MT * CK * 2, B_BYTES = BN * CK * 2;
+    constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
+    constexpr int ROW_BYTES = CK * ES;
+    constexpr uint32_t A_BYTES = 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
-    constexpr uint32_t IDESC = ptx::make_idesc(128, BN, 1, 1);
-    constexpr int ROW_BYTES = CK * 2;
+    constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -239,12 +255,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ptx::tc_fence_after();
                     uint32_t a0 = ptx::smem_u32(sA + stage * A_STRIDE), b0 = ptx::smem_u32(sB + stage * B_STRIDE);
 #pragma unroll
-                    for (int k = 0; k < CK / 16; ++k) {
+                    for (int k = 0; k < ROW_BYTES / 32; ++k) {
                         uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
 #pragma unroll
                         for (int m = 0; m < MT; ++m) {
                             uint64_t ad = ptx::smem_desc(a0 + m * 128 * ROW_BYTES + k * 32, ROW_BYTES);
-                            ptx::mma_bf16(d + m * BN, ad, bd, IDESC, (kb | k) != 0);
+                            if (F8) ptx::mma_f8(d + m * BN, ad, bd, IDESC, (kb | k) != 0);
+                            else ptx::mma_bf16(d + m * BN, ad, bd, IDESC, (kb | k) != 0);
                         }
                     }
                     issued_any = true;
@@ -360,21 +377,35 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int oy = gy, ox = gx;
                 if (p.mode == MODE_T || p.mode == MODE_T3) { oy = 2 * gy + (cph >> 1); ox = 2 * gx + (cph & 1); }
                 if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co) {
-                    __nv_bfloat162 h[8];
+                    float v[16];
+                    float vmax = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float a = __uint_as_float(r[2 * j]) + __ldg(p.bias + co0 + 2 * j);
-                        float b = __uint_as_float(r[2 * j + 1]) + __ldg(p.bias + co0 + 2 * j + 1);
-                        if (p.relu) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
-                        h[j] = __floats2bfloat162_rn(a, b);
+                    for (int j = 0; j < 16; ++j) {
+                        float sc = p.acc_scale ? __ldg(p.acc_scale + co0 + j) : 1.f;
+                        float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + co0 + j);
+                        v[j] = p.relu ? fmaxf(a, 0.f) : a;
+                        vmax = fmaxf(vmax, fabsf(v[j]));
                     }
+                    if (p.amax) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
                     size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
-                    uint4 w0, w1;
-                    memcpy(&w0, &h[0], 16);
-                    memcpy(&w1, &h[4], 16);
-                    bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + co0;
-                    reinterpret_cast<uint4 *>(dst)[0] = w0;
-                    reinterpret_cast<uint4 *>(dst)[1] = w1;
+                    if (p.out_fp8) {
+                        uint8_t q8[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) q8[j] = to_e4m3(v[j] * p.out_q);
+                        uint4 w;
+                        memcpy(&w, q8, 16);
+                        *reinterpret_cast<uint4 *>((uint8_t *)p.out + pix * p.out_cs + p.out_coff + co0) = w;
+                    } else {
+                        __nv_bfloat162 h[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        uint4 w0, w1;
+                        memcpy(&w0, &h[0], 16);
+                        memcpy(&w1, &h[4], 16);
+                        bf16 *dst = (bf16 *)p.out + pix * p.out_cs + p.out_coff + co0;
+                        reinterpret_cast<uint4 *>(dst)[0] = w0;
+                        reinterpret_cast<uint4 *>(dst)[1] = w1;
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -426,6 +457,8 @@ int get_encoder() {
     return FVV_OK;
 }
 
+bool g_encode_u8 = false; // next encode() describes 1-byte (FP8) elements
+
 CUtensorMapSwizzle swz_for(int ck_bytes) {
     return ck_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                            : (ck_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
@@ -434,7 +467,8 @@ CUtensorMapSwizzle swz_for(int ck_bytes) {
 int encode(CUtensorMap *m, int rank, void *base, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
            const cuuint32_t *box, int ck_bytes) {
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, base, dims, strides_bytes, box, es,
+    CUresult r = g_encode(m, g_encode_u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, base,
+                          dims, strides_bytes, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz_for(ck_bytes), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -472,8 +506,9 @@ int mt_for(int bn, int ck) { return ck == 64 && bn == 128 ? 2 : 1; }
 // configs put several CTAs on an SM (their TMEM columns and shared memory allow
 // it), so more TMA copies are in flight per SM: those layers are bound by copy latency.
 constexpr uint32_t kSmemBudget = 220 * 1024; // per SM, for all resident CTAs
-template <int BN, int CK, int MT> struct Cfg {
-    static constexpr uint32_t A = ((128 * MT * CK * 2) + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
+template <int BN, int CK, int MT, int F8 = 0> struct Cfg {
+    static constexpr uint32_t ES = F8 ? 1 : 2;
+    static constexpr uint32_t A = ((128 * MT * CK * ES) + 1023) & ~1023u, B = ((BN * CK * ES) + 1023) & ~1023u;
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048) / (A + B)); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
@@ -485,11 +520,11 @@ template <int BN, int CK, int MT> struct Cfg {
 
 int g_num_sms = 0;
 
-template <int BN, int CK>
+template <int BN, int CK, int F8 = 0>
 int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
-    constexpr int MT = (CK == 64 && BN == 128) ? 2 : 1; // = mt_for(BN, CK)
-    using C = Cfg<BN, CK, MT>;
-    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS>;
+    constexpr int MT = (!F8 && CK == 64 && BN == 128) ? 2 : 1; // = mt_for(BN, CK)
+    using C = Cfg<BN, CK, MT, F8>;
+    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -508,7 +543,13 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, 
     return FVV_OK;
 }
 
-int dispatch(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p,
+             cudaStream_t st) {
+    if (f8) {
+        if (bn == 256 && ck == 128) return launch_cfg<256, 128, 1>(ma, mb, p, st);
+        set_error("no FP8 tensor-core kernel for N=%d, CK=%d", bn, ck);
+        return FVV_EINVAL;
+    }
 #define FVV_CASE(BN_, CK_) \
     if (bn == BN_ && ck == CK_) return launch_cfg<BN_, CK_>(ma, mb, p, st);
     FVV_CASE(16, 16) FVV_CASE(16, 64) FVV_CASE(32, 16) FVV_CASE(32, 32) FVV_CASE(32, 64)
@@ -523,6 +564,8 @@ int dispatch(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb, const
 
 // Pack every layer's weights as bf16 [G][Co_pad][Ci_pad] (G = 9 taps, or 4 phases
 // x 4 taps for the transposed conv) and build its B tensor map.
+int tc_prepare_fp8(fvv_interp *h, const float *blob);
+
 int tc_prepare(fvv_interp *h, const float *blob) {
     FVV_TRY(get_encoder());
     if (h->o.pad_mode != FVV_PAD_ZERO) {
@@ -585,6 +628,48 @@ int tc_prepare(fvv_interp *h, const float *blob) {
         static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
         FVV_TRY(encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, ck * 2));
     }
+    if (h->o.precision == FVV_FP8) FVV_TRY(tc_prepare_fp8(h, blob));
+    return FVV_OK;
+}
+
+// E4M3 weights of the FP8 layers: per output channel s_w = max |w| / 448 over
+// its taps and input channels, codes = RNE-satfinite(w / s_w), layout [9][C_out][C_in].
+int tc_prepare_fp8(fvv_interp *h, const float *blob) {
+    size_t off = 0;
+    for (int i = 0; i < kNumLayers; ++i) {
+        const LayerDef &L = kLayers[i];
+        const float *w = blob + off;
+        off += (size_t)L.ci * L.co * (L.kind == K_CONV ? 9 : 16) + L.co;
+        if (!fp8_layer(i)) continue;
+        std::vector<float> sw(L.co);
+        std::vector<uint8_t> pk((size_t)9 * L.co * L.ci);
+        for (int co = 0; co < L.co; ++co) {
+            float m = 0.f;
+            for (int k = 0; k < L.ci * 9; ++k) m = fmaxf(m, fabsf(w[(size_t)co * L.ci * 9 + k]));
+            sw[co] = m > 0.f ? m / 448.f : 1.f;
+        }
+        for (int tap = 0; tap < 9; ++tap)
+            for (int co = 0; co < L.co; ++co)
+                for (int ci = 0; ci < L.ci; ++ci)
+                    pk[((size_t)tap * L.co + co) * L.ci + ci] = (uint8_t)__nv_cvt_float_to_fp8(
+                        w[((size_t)co * L.ci + ci) * 9 + tap] / sw[co], __NV_SATFINITE, __NV_E4M3);
+        TcWeights &tw = h->tc8[i];
+        tw.ci_pad = L.ci;
+        tw.co_pad = L.co;
+        FVV_TRY(dalloc(h, &tw.w, pk.size()));
+        FVV_CHECK_CUDA(cudaMemcpy(tw.w, pk.data(), pk.size(), cudaMemcpyHostToDevice));
+        FVV_TRY(dalloc(h, (void **)&h->q_acc[i], L.co * sizeof(float)));
+        h->s_w[i] = sw;
+        cuuint64_t dims[3] = {(cuuint64_t)L.ci, (cuuint64_t)L.co, 9};
+        cuuint64_t strides[2] = {(cuuint64_t)L.ci, (cuuint64_t)L.ci * L.co};
+        cuuint32_t box[3] = {128, (cuuint32_t)L.co, 1};
+        g_encode_u8 = true;
+        int rc = encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, 128);
+        g_encode_u8 = false;
+        FVV_TRY(rc);
+    }
+    FVV_TRY(dalloc(h, (void **)&h->d_amax, kNumLayers * sizeof(float)));
+    FVV_CHECK_CUDA(cudaMemset(h->d_amax, 0, kNumLayers * sizeof(float)));
     return FVV_OK;
 }
 
@@ -593,9 +678,13 @@ bool tc_all_phases(int li) { return kLayers[li].kind == K_CONVT && 4 * kLayers[l
 int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win, void *out,
             int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi) {
     const LayerDef &L = kLayers[li];
-    const TcWeights &tw = h->tc[li];
-    const int cip = tw.ci_pad, ck = ck_of(cip), bn = tw.co_pad;
-    if (in_cs % 8 || in_coff % 8 || in_coff + cip > in_cs) {
+    // FP8 once calibrated (calibration itself runs every layer in BF16)
+    const bool f8_on = h->o.precision == FVV_FP8 && h->fp8_ready && !h->calibrating;
+    const bool f8 = f8_on && fp8_layer(li);
+    const TcWeights &tw = f8 ? h->tc8[li] : h->tc[li];
+    const int es = f8 ? 1 : 2;                       // input element bytes
+    const int cip = tw.ci_pad, ck = f8 ? 128 : ck_of(cip), bn = tw.co_pad;
+    if (in_cs % (16 / es) || in_coff % (16 / es) || in_coff + cip > in_cs) {
         set_error("layer %s: input slice (cs %d, off %d, %d ch) not TMA-aligned", L.name, in_cs, in_coff, cip);
         return FVV_EINVAL;
     }
@@ -623,7 +712,12 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.taps = p.mode == MODE_T ? 4 : 9;
     p.in_cs = in_cs; p.in_coff = in_coff;
     p.co = L.co; p.relu = L.relu; p.out_f32 = out_f32 ? 1 : 0;
-    p.vec_ok = (out_cs % 8 == 0 && out_coff % 8 == 0 && ((uintptr_t)out % 16) == 0) ? 1 : 0;
+    p.acc_scale = f8 ? h->q_acc[li] : nullptr;
+    p.out_fp8 = f8_on && feeds_fp8(li) && !out_f32 ? 1 : 0;
+    p.out_q = h->q_out[li];
+    p.amax = h->calibrating && feeds_fp8(li) ? h->d_amax + li : nullptr;
+    const int ovec = p.out_fp8 ? 16 : 8;             // elements per 16 bytes of output
+    p.vec_ok = (out_cs % ovec == 0 && out_coff % ovec == 0 && ((uintptr_t)out % 16) == 0) ? 1 : 0;
     p.out = out; p.out_cs = out_cs; p.out_coff = out_coff;
     p.bias = h->bias + h->b_off[li];
     p.err = h->d_err;
@@ -638,20 +732,25 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
 
     CUtensorMap ma;
     const int tw_ = 1 << s.tw_log, th_ = 1 << s.th_log;
+    const cuuint64_t e = (cuuint64_t)es;
+    g_encode_u8 = f8;
+    int rc;
     if (p.mode == MODE_S2) {
-        if (Hin % 2 || Win % 2) { set_error("stride-2 layer %s needs even input size", L.name); return FVV_ESHAPE; }
+        if (Hin % 2 || Win % 2) { g_encode_u8 = false; set_error("stride-2 layer %s needs even input size", L.name); return FVV_ESHAPE; }
         cuuint64_t dims[5] = {(cuuint64_t)2 * in_cs, (cuuint64_t)Win / 2, 2, (cuuint64_t)Hin / 2, (cuuint64_t)N};
-        cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * 2, (cuuint64_t)Win * in_cs * 2,
-                                 (cuuint64_t)2 * Win * in_cs * 2, (cuuint64_t)Hin * Win * in_cs * 2};
+        cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * e, (cuuint64_t)Win * in_cs * e,
+                                 (cuuint64_t)2 * Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
         cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)tw_, 1, (cuuint32_t)th_, 1};
-        FVV_TRY(encode(&ma, 5, (void *)in, dims, strides, box, ck * 2));
+        rc = encode(&ma, 5, (void *)in, dims, strides, box, ck * es);
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
-        cuuint64_t strides[3] = {(cuuint64_t)in_cs * 2, (cuuint64_t)Win * in_cs * 2, (cuuint64_t)Hin * Win * in_cs * 2};
+        cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
         cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)tw_, (cuuint32_t)th_, 1};
-        FVV_TRY(encode(&ma, 4, (void *)in, dims, strides, box, ck * 2));
+        rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
-    return dispatch(bn, ck, ma, *(const CUtensorMap *)tw.map, p, st);
+    g_encode_u8 = false;
+    FVV_TRY(rc);
+    return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, p, st);
 }
 
 } // namespace fvv

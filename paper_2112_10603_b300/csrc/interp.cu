@@ -336,7 +336,11 @@ static void drop_graphs(fvv_interp *h) {
 // (captured on first use; every buffer it touches is fixed per handle and the
 // per-call data -- view table, camera and output pointers -- is read from device slots).
 static int dispatch_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
-    if (!h->o.graphs || h->profiling) return interp_forward(h, n_cams, nv, st);
+    if (h->o.precision == FVV_FP8 && !h->fp8_ready && !h->calibrating) {
+        set_error("FP8 handle: call fvv_calibrate_fp8 before running");
+        return FVV_EINVAL;
+    }
+    if (!h->o.graphs || h->profiling || h->calibrating) return interp_forward(h, n_cams, nv, st);
     long long key = ((long long)n_cams * 65536 + nv) * 2 + (h->skip_cams ? 1 : 0);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
@@ -548,6 +552,57 @@ int fvv_interp_layer_stats(fvv_interp *h, double *ms, double *flops, int *launch
         if (launches) launches[r.layer] += 1;
     }
     prof_reset(h);
+    return FVV_OK;
+}
+
+// ---- FP8 calibration ---------------------------------------------------------
+
+int fvv_calibrate_fp8(fvv_interp *h, const float *frames, int n_pairs, void *stream) {
+    clear_error();
+    if (!h || !frames || n_pairs < 1) { set_error("bad calibration arguments"); return FVV_EINVAL; }
+    if (h->o.precision != FVV_FP8) { set_error("the handle was not created with FVV_FP8"); return FVV_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t img = (size_t)h->H * h->W * 3;
+    const int nv = h->o.max_views < 3 ? h->o.max_views : 3;
+    const float ts[3] = {0.25f, 0.5f, 0.75f};
+    if (!h->d_out) {
+        FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
+        FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
+    }
+    drop_graphs(h);
+    h->calibrating = 1; // every layer in BF16, producers of FP8 inputs record max |output|
+    FVV_CHECK_CUDA(cudaMemsetAsync(h->d_amax, 0, kNumLayers * sizeof(float), st));
+    int rc = FVV_OK;
+    for (int p = 0; p < n_pairs && rc == FVV_OK; ++p)
+        rc = fvv_interp_run(h, frames + 2 * p * img, frames + (2 * p + 1) * img, ts, nv, h->d_out, stream);
+    h->calibrating = 0;
+    if (rc != FVV_OK) return rc;
+    float amax[kNumLayers];
+    FVV_CHECK_CUDA(cudaStreamSynchronize(st));
+    FVV_CHECK_CUDA(cudaMemcpy(amax, h->d_amax, sizeof amax, cudaMemcpyDeviceToHost));
+    // s_a of an FP8 layer's input = max |producer output| / 448 (E4M3's largest finite)
+    for (int i = 0; i < kNumLayers; ++i) {
+        if (!fp8_layer(i)) continue;
+        float sa = amax[i - 1] > 0.f ? amax[i - 1] / 448.f : 1.f;
+        h->s_a[i] = sa;
+        h->q_out[i - 1] = 1.f / sa;
+        std::vector<float> acc(h->s_w[i].size());
+        for (size_t c = 0; c < acc.size(); ++c) acc[c] = sa * h->s_w[i][c];
+        FVV_CHECK_CUDA(cudaMemcpy(h->q_acc[i], acc.data(), acc.size() * 4, cudaMemcpyHostToDevice));
+    }
+    h->fp8_ready = 1;
+    drop_graphs(h);
+    return FVV_OK;
+}
+
+int fvv_interp_fp8_scales(fvv_interp *h, int layer, float *s_a, float *s_w, int n) {
+    clear_error();
+    if (!h || layer < 0 || layer >= kNumLayers || !fp8_layer(layer) || h->o.precision != FVV_FP8) {
+        set_error("not an FP8 layer of an FP8 handle"); return FVV_EINVAL;
+    }
+    if (!h->fp8_ready) { set_error("not calibrated"); return FVV_EINVAL; }
+    if (s_a) *s_a = h->s_a[layer];
+    for (int c = 0; s_w && c < n && c < (int)h->s_w[layer].size(); ++c) s_w[c] = h->s_w[layer][c];
     return FVV_OK;
 }
 

@@ -85,6 +85,15 @@ struct fvv_interp {
     // set by the server while the frames (and so the pyramid and ContextNet features
     // already in this handle's workspace) are those of its previous run
     int skip_cams = 0;
+    // FP8 (E4M3) path for the 256-channel VIB convs: weights with per-output-channel
+    // scales s_w, activations with per-tensor scales s_a from calibration
+    fvv::TcWeights tc8[fvv::kNumLayers];
+    std::vector<float> s_w[fvv::kNumLayers];  // host copy of the weight scales
+    float s_a[fvv::kNumLayers] = {};          // input scale of each FP8 layer
+    float q_out[fvv::kNumLayers] = {};        // 1 / s_a of the consumer (producers of FP8 inputs)
+    float *q_acc[fvv::kNumLayers] = {};       // device: s_a * s_w[co]
+    float *d_amax = nullptr;                  // device: max |output| per layer while calibrating
+    int fp8_ready = 0, calibrating = 0;
 };
 
 namespace fvv {
@@ -94,4 +103,8 @@ int tc_prepare(fvv_interp *h, const float *blob);
 int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
             void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
+// FP8 layers: the six 256 -> 256 convs of every VIBlock; their producers are the
+// layer before (c1 or the previous m) and write E4M3 codes.
+inline bool fp8_layer(int li) { return li < kCtx && li % 10 >= 2 && li % 10 <= 7; }
+inline bool feeds_fp8(int li) { return li < kCtx && li % 10 >= 1 && li % 10 <= 6; }
 } // namespace fvv
