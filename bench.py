@@ -290,6 +290,26 @@ def run_serve(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def rank_pair_seed(rank: int) -> int:
+    """Each rank synthesises its own camera pair (weak scaling: the work per GPU is fixed)."""
+    return SCENE_SEED + rank
+
+
+def reduce_ranks(ms_local: float, views_local: int, dist=None, device="cpu"):
+    """(slowest rank's ms, whole-job views/s): the only cross-rank step of the bench.
+    Views of different pairs are independent, so no data moves between ranks."""
+    import torch
+    if dist is None:
+        return ms_local, views_local / (ms_local / 1e3)
+    t = torch.tensor([ms_local, float(views_local)], dtype=torch.float64, device=device)
+    mx = t[:1].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t[1:].clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    t_max = float(mx.item())
+    return t_max, float(tot.item()) / (t_max / 1e3)
+
+
 def config_dict(args):
     return {"workload": f"1 camera pair 1920x1080 (padded 1920x1088), {len(TS)} views t=k/{len(TS) + 1} per step",
             "H": H, "W": W, "views_per_step": len(TS), "precision": args.precision,
@@ -339,7 +359,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     blob = weights.he_init(WEIGHT_SEED)
-    left, right = scene.stereo_pair(SCENE_SEED + rank, H, W, MAX_DISP)
+    left, right = scene.stereo_pair(rank_pair_seed(rank), H, W, MAX_DISP)
     L = torch.from_numpy(left).cuda()
     R = torch.from_numpy(right).cuda()
     prec = {"bf16": fvv.FVV_BF16, "fp32": fvv.FVV_FP32, "fp8": fvv.FVV_FP8}[args.precision]
@@ -384,13 +404,7 @@ def main():
     launches = it.last_launches * args.steps
     lms, lfl, lln = fvv.fvv_interp_layer_stats(it.h)
     fvv.fvv_interp_profile(it.h, False)
-    t_max = ms_total
-    if dist:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    views = len(TS) * args.steps * world
-    value = views / (t_max / 1e3)
+    t_max, value = reduce_ranks(ms_total, len(TS) * args.steps, dist, device="cuda")
 
     if args.no_extras:
         if rank == 0:

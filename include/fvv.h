@@ -55,8 +55,12 @@ typedef struct {
     int precision; /* FVV_FP32 (SIMT FP32 FMA), FVV_BF16 (tcgen05, FP32 accumulate), FVV_FP8 */
     int pad_mode;  /* FVV_PAD_ZERO: zero conv padding, border-clamped sampling;
                       FVV_PAD_CIRCULAR: everything wraps (needs H, W multiples of 16) */
-    int t_mode;    /* FVV_T_DIRECT: t plane = t;  FVV_T_RECURSIVE: dyadic stacking of
-                      midpoint views (t must be k / 2^n) */
+    int t_mode;    /* FVV_T_DIRECT: the t plane of every VIBlock = t;
+                      FVV_T_RECURSIVE: the paper's dense views (Sec. 4.2): only the
+                      midpoint network (t plane 0.5) is run, recursively — the view at
+                      t = k / 2^n (k odd, n <= 12) is the midpoint of its neighbours at
+                      spacing 1 / 2^n; n stages give 2^n - 1 views.  fvv_interp_run
+                      only; every dyadic level is one batched forward */
     int max_views; /* views per run call the workspace is sized for (>= 1) */
     int max_cams;  /* cameras per batched call (>= 2) */
     int graphs;    /* 1: each run replays a CUDA graph captured on first use for its

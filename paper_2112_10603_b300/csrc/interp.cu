@@ -361,6 +361,91 @@ static int dispatch_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) 
     return FVV_OK;
 }
 
+// Dense views by stacking the midpoint network (the paper's recursive scheme, Sec.
+// 4.2 and supplement S.3): the view at t = k / 2^n (k odd) is the midpoint view of
+// its two neighbours at spacing 1 / 2^n, each of which is a camera (t = 0, 1) or an
+// earlier such view.  Levels run in order of depth; every level is one batched
+// forward over all of its midpoints (t plane 0.5), with the known images of the
+// level as the "cameras" and each midpoint's two neighbours adjacent among them.
+static int run_recursive(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
+                         float *out, cudaStream_t st) {
+    const int kMaxDepth = 12;
+    // requested positions as (numerator, depth) with an odd numerator
+    std::map<long long, int> need;  // numerator at depth kMaxDepth -> depth
+    std::vector<long long> req(n_views);
+    for (int i = 0; i < n_views; ++i) {
+        double x = (double)t[i] * (1 << kMaxDepth);
+        long long k = (long long)llround(x);
+        if (fabs(x - (double)k) > 1e-3 || k <= 0 || k >= (1 << kMaxDepth)) {
+            set_error("recursive t mode: t[%d] = %g is not k / 2^n with 0 < t < 1, n <= %d", i, t[i], kMaxDepth);
+            return FVV_EINVAL;
+        }
+        req[i] = k;
+    }
+    // close under "both neighbours known": a position of depth d needs k -/+ 2^(D - d)
+    std::vector<long long> stack(req.begin(), req.end());
+    while (!stack.empty()) {
+        long long k = stack.back();
+        stack.pop_back();
+        if (need.count(k)) continue;
+        int tz = __builtin_ctzll((unsigned long long)k);
+        int depth = kMaxDepth - tz;
+        need[k] = depth;
+        long long step = 1ll << tz;
+        for (long long nb : {k - step, k + step})
+            if (nb > 0 && nb < (1ll << kMaxDepth)) stack.push_back(nb);
+    }
+    const size_t img = (size_t)h->H * h->W * 3;
+    if ((int)need.size() > h->rec_cap) {
+        if ((int)need.size() + 2 > h->o.max_cams) {
+            set_error("recursive t mode needs %zu generated views; max_cams is %d", need.size(), h->o.max_cams);
+            return FVV_ESHAPE;
+        }
+        FVV_TRY(dalloc_t(h, &h->rec_buf, need.size() * img * 4));
+        h->rec_cap = (int)need.size();
+    }
+    std::map<long long, const float *> known;  // position -> image
+    known[0] = left;
+    known[1ll << kMaxDepth] = right;
+    std::map<long long, int> slot;
+    int next_slot = 0, launches = 0;
+    for (int d = 1; d <= kMaxDepth; ++d) {
+        std::vector<long long> mids;
+        for (auto &kv : need)
+            if (kv.second == d) mids.push_back(kv.first);
+        if (mids.empty()) continue;
+        if ((int)mids.size() > h->o.max_views) { set_error("recursive level wider than max_views"); return FVV_ESHAPE; }
+        // cameras of this level: the known images in position order; midpoint m sits
+        // between its two neighbours, which are adjacent in that order
+        std::vector<const float *> cams;
+        std::map<long long, int> cam_of;
+        for (auto &kv : known) { cam_of[kv.first] = (int)cams.size(); cams.push_back(kv.second); }
+        std::vector<int> cl, cr;
+        std::vector<float> tv;
+        long long step = 1ll << (kMaxDepth - d);
+        for (long long m : mids) {
+            cl.push_back(cam_of.at(m - step));
+            cr.push_back(cam_of.at(m + step));
+            tv.push_back(0.5f);
+        }
+        float *dst = h->rec_buf + (size_t)next_slot * img;
+        FVV_TRY(upload_tables(h, cams.data(), (int)cams.size(), cl.data(), cr.data(), tv.data(), (int)mids.size(), dst,
+                              st));
+        FVV_TRY(dispatch_forward(h, (int)cams.size(), (int)mids.size(), st));
+        launches += h->last_launches;
+        for (size_t i = 0; i < mids.size(); ++i) {
+            slot[mids[i]] = next_slot + (int)i;
+            known[mids[i]] = h->rec_buf + (size_t)(next_slot + i) * img;
+        }
+        next_slot += (int)mids.size();
+    }
+    for (int i = 0; i < n_views; ++i)
+        FVV_CHECK_CUDA(cudaMemcpyAsync(out + (size_t)i * img, h->rec_buf + (size_t)slot.at(req[i]) * img, img * 4,
+                                       cudaMemcpyDeviceToDevice, st));
+    h->last_launches = launches;
+    return FVV_OK;
+}
+
 static int check_t(const float *t, int n) {
     for (int i = 0; i < n; ++i)
         if (!(t[i] >= 0.f && t[i] <= 1.f)) { set_error("t[%d] = %g outside [0, 1]", i, t[i]); return FVV_EINVAL; }
@@ -409,6 +494,9 @@ int fvv_interp_create(const float *weights, size_t n_floats, int H, int W, const
         set_error("max_views in [1, 1024] and max_cams in [2, 64] required"); return FVV_ESHAPE;
     }
     fvv_interp *h = new fvv_interp();
+    // recursive t mode: each level's "cameras" are the images known so far
+    if (o.t_mode == FVV_T_RECURSIVE && o.max_cams < 2 * o.max_views + 2)
+        o.max_cams = 2 * o.max_views + 2 < 64 ? 2 * o.max_views + 2 : 64;
     h->H = H; h->W = W; h->o = o;
     for (int i = 0; i < kNumLayers; ++i) h->tile_tw[i] = -1;
     h->Hp = (H + 15) / 16 * 16; h->Wp = (W + 15) / 16 * 16;
@@ -427,6 +515,7 @@ int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const f
     }
     FVV_TRY(check_t(t, n_views));
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->o.t_mode == FVV_T_RECURSIVE) return run_recursive(h, left, right, t, n_views, out, st);
     std::vector<int> cl(n_views, 0), cr(n_views, 1);
     const float *cams[2] = {left, right};
     FVV_TRY(upload_tables(h, cams, 2, cl.data(), cr.data(), t, n_views, out, st));
@@ -460,6 +549,9 @@ int fvv_interp_run_batch(fvv_interp *h, const float *const *cams, int n_cams, co
     if (!h || !cams || !pair_left || !view_offsets || !t || !out) { set_error("NULL argument"); return FVV_EINVAL; }
     if (n_cams < 2 || n_cams > h->o.max_cams || n_pairs < 1) { set_error("n_cams/n_pairs out of range"); return FVV_ESHAPE; }
     if (view_offsets[0] != 0) { set_error("view_offsets[0] must be 0"); return FVV_EINVAL; }
+    if (h->o.t_mode == FVV_T_RECURSIVE && !h->skip_cams) {
+        set_error("recursive t mode runs through fvv_interp_run (one pair)"); return FVV_EINVAL;
+    }
     int nv = view_offsets[n_pairs];
     if (nv < 1 || nv > h->o.max_views) { set_error("total views %d outside [1, %d]", nv, h->o.max_views); return FVV_ESHAPE; }
     FVV_TRY(check_t(t, nv));

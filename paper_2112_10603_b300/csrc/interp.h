@@ -94,6 +94,9 @@ struct fvv_interp {
     float *q_acc[fvv::kNumLayers] = {};       // device: s_a * s_w[co]
     float *d_amax = nullptr;                  // device: max |output| per layer while calibrating
     int fp8_ready = 0, calibrating = 0;
+    // recursive t mode: generated intermediate views
+    float *rec_buf = nullptr;
+    int rec_cap = 0;
 };
 
 namespace fvv {
