@@ -12,6 +12,8 @@
 // phase for the transposed conv.  Inputs/outputs may be channel slices of wider
 // tensors (pixel stride cs, channel offset coff), which is how concatenations
 // are formed without copies.
+#include <cstring>
+
 #include "common.h"
 #include "kernels.h"
 
@@ -182,7 +184,72 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
     }
 }
 
+// RefineNet's last layer (Conv2d 16 -> 3, then Sigmoid, Table 3) fused with the
+// residual output: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped.  Only
+// 3 output channels: a tensor-core tile would use 3 of its 16 columns, so this is
+// a shared-memory-tiled direct conv.  A block computes 32 x 8 output pixels of one
+// view from an (8 + 2) x (32 + 2) input patch (16 bf16 channels per pixel, stored
+// with a 9-word pitch so that neighbouring pixels fall in different banks).
+constexpr int OC_TX = 32, OC_TY = 8, OC_PITCH = 9; // words per pixel in shared memory
+
+__global__ void __launch_bounds__(OC_TX *OC_TY)
+out_conv_fused_kernel(const bf16 *in, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
+                      float *const *outp, int H, int W) {
+    __shared__ uint32_t tile[(OC_TY + 2) * (OC_TX + 2) * OC_PITCH];
+    __shared__ float ws[144 * 3];
+    __shared__ float bs[3];
+    const int tid = threadIdx.x, n = blockIdx.z;
+    const int x0 = blockIdx.x * OC_TX, y0 = blockIdx.y * OC_TY;
+    for (int i = tid; i < 144 * 3; i += blockDim.x) ws[i] = wp[i];
+    if (tid < 3) bs[tid] = bias[tid];
+    const int npx = (OC_TY + 2) * (OC_TX + 2);
+    for (int i = tid; i < npx * 2; i += blockDim.x) {
+        int p = i >> 1, half = i & 1;
+        int iy = y0 - 1 + p / (OC_TX + 2), ix = x0 - 1 + p % (OC_TX + 2);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (iy >= 0 && iy < Hp && ix >= 0 && ix < Wp)
+            v = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)n * Hp + iy) * Wp + ix) * 16) + half);
+        uint32_t *d = tile + p * OC_PITCH + half * 4;
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __syncthreads();
+    const int tx = tid % OC_TX, ty = tid / OC_TX;
+    const int oy = y0 + ty, ox = x0 + tx;
+    if (oy >= H || ox >= W) return;
+    float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t *px = tile + ((ty + tap / 3) * (OC_TX + 2) + tx + tap % 3) * OC_PITCH;
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2) {
+            __nv_bfloat162 hv;
+            memcpy(&hv, px + c2, 4);
+            float2 v = __bfloat1622float2(hv);
+            const float *wr = ws + (tap * 16 + 2 * c2) * 3;
+#pragma unroll
+            for (int co = 0; co < 3; ++co) acc[co] = fmaf(v.y, wr[3 + co], fmaf(v.x, wr[co], acc[co]));
+        }
+    }
+    const size_t q = ((size_t)n * Hp + oy) * Wp + ox;
+    float *out = *outp + (((size_t)n * H + oy) * W + ox) * 3;
+#pragma unroll
+    for (int co = 0; co < 3; ++co) {
+        float z = acc[co] + bs[co];
+        float r = 2.f / (1.f + expf(-z)) - 1.f;
+        out[co] = fminf(fmaxf(__ldg(ib + q * 3 + co) + r, 0.f), 1.f);
+    }
+}
+
 } // namespace
+
+int launch_out_conv_fused(const bf16 *in, int N, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
+                          float *const *outp, int H, int W, cudaStream_t st) {
+    dim3 grid(ceil_div(W, OC_TX), ceil_div(H, OC_TY), N);
+    out_conv_fused_kernel<<<grid, OC_TX * OC_TY, 0, st>>>(in, Hp, Wp, wp, bias, ib, outp, H, W);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
 
 int launch_conv_c3(const ConvArgs &a, bool out_bf16, cudaStream_t st) {
     if (a.Ci != 3 || a.Co != 16 || a.kind != K_CONV) { set_error("conv_c3: 3 -> 16 conv only"); return FVV_EINVAL; }

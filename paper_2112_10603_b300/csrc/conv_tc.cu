@@ -68,7 +68,7 @@ __device__ __forceinline__ uint8_t to_e4m3(float v) {
 }
 
 struct __align__(8) Bars {
-    uint64_t full[8], empty[8], tmem_full[2], tmem_empty[2], drain;
+    uint64_t full[16], empty[16], tmem_full[2], tmem_empty[2], drain;
     uint32_t tmem_base;
     int abort;
 };
@@ -144,13 +144,18 @@ template <int BN, int MT> struct AccCfg {
 
 // F8 = 1: E4M3 operands (kind::f8f6f4, K = 32 per MMA), else BF16 (kind::f16, K = 16);
 // either way one MMA consumes 32 bytes of every operand row.
-template <int BN, int CK, int MT, int STAGES, int CTAS, int F8>
+// HALO = 1 (stride-1 3x3 taps, 1 x 128-pixel tiles, 128-byte rows): one TMA box of
+// 130 pixels per (row tap ky, channel block) serves the three column taps kx, whose
+// A operands start 0, 1, 2 rows into it; A boxes (STAGES ring) and B slices
+// (STAGES_B ring) are pipelined separately.  K order is (ky, block, kx) on both paths.
+template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
+    constexpr uint32_t A_BYTES = HALO ? 130 * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
+    static_assert(!HALO || (ROW_BYTES == 128 && MT == 1 && STAGES + STAGES_B <= 16), "halo config");
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -159,13 +164,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_STRIDE;
-    Bars *bars = (Bars *)(sB + STAGES * B_STRIDE);
+    Bars *bars = (Bars *)(sB + (HALO ? STAGES_B : STAGES) * B_STRIDE);
     volatile int *abort = &bars->abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        // halo: full/empty[0, STAGES) = A ring, [STAGES, STAGES + STAGES_B) = B ring
+        for (int s = 0; s < (HALO ? STAGES + STAGES_B : STAGES); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
         }
@@ -192,7 +198,51 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0) {
+        if (lane == 0 && HALO) {
+            int sa = 0, sb = 0;
+            uint32_t pa = 0, pb = 0;
+            long long issued_a = 0, issued_b = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+                int ph, n, y0, x0;
+                tile_coords(p, t, ph, n, y0, x0);
+                for (int ky = 0; ky < 3 && !stop; ++ky)
+                    for (int c = 0; c < p.nck && !stop; ++c) {
+                        if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
+                        uint32_t fa = ptx::smem_u32(&bars->full[sa]);
+                        ptx::mbar_arrive_expect_tx(fa, A_BYTES);
+                        ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
+                                         y0 + ky - 1, n);
+                        ++issued_a;
+                        if (++sa == STAGES) { sa = 0; pa ^= 1; }
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const int slot = STAGES + sb;
+                            if (!wait_bar(ptx::smem_u32(&bars->empty[slot]), pb ^ 1, abort, p.err, 1)) { stop = true; break; }
+                            uint32_t fbb = ptx::smem_u32(&bars->full[slot]);
+                            ptx::mbar_arrive_expect_tx(fbb, B_BYTES);
+                            ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
+                            ++issued_b;
+                            if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
+                        }
+                    }
+            }
+            if (*abort || stop) {
+                // let every copy still in flight land before the CTA exits
+                for (int s = 0; s < STAGES && s < issued_a; ++s) {
+                    long long k = issued_a - 1 - s;
+                    long long t0 = clock64();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full[k % STAGES]), (uint32_t)((k / STAGES) & 1)) &&
+                           clock64() - t0 < kWaitCycles) {}
+                }
+                for (int s = 0; s < STAGES_B && s < issued_b; ++s) {
+                    long long k = issued_b - 1 - s;
+                    long long t0 = clock64();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full[STAGES + k % STAGES_B]),
+                                               (uint32_t)((k / STAGES_B) & 1)) &&
+                           clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        } else if (lane == 0) {
             int stage = 0;
             uint32_t phase_bit = 0;
             long long issued = 0;
@@ -206,7 +256,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ptx::mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES);
                     uint32_t da = ptx::smem_u32(sA + stage * A_STRIDE), db = ptx::smem_u32(sB + stage * B_STRIDE);
                     if (p.mode == MODE_S1 || p.mode == MODE_T3) {
-                        int ky = tap / 3, kx = tap - 3 * (tap / 3);
+                        // K order (ky, channel block, kx): the same as the halo path
+                        const int ky = kb / (3 * p.nck), r = kb - ky * 3 * p.nck, kx = r % 3;
+                        c0 = (r / 3) * CK;
+                        tap = ky * 3 + kx;
                         ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1, y0 + ky - 1, n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
                     } else if (p.mode == MODE_S2) {
@@ -239,7 +292,56 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0) {
+        if (lane == 0 && HALO) {
+            int sa = 0, sb = 0;
+            uint32_t pa = 0, pb = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem + acc * BN;
+                bool ok = true;
+                uint32_t accumulate = 0;
+                for (int ky = 0; ky < 3 && ok; ++ky)
+                    for (int c = 0; c < p.nck && ok; ++c) {
+                        if (!wait_bar(ptx::smem_u32(&bars->full[sa]), pa, abort, p.err, 3)) { ok = false; break; }
+                        ptx::tc_fence_after();
+                        const uint32_t a0 = ptx::smem_u32(sA + sa * A_STRIDE);
+                        for (int kx = 0; kx < 3; ++kx) {
+                            if (!wait_bar(ptx::smem_u32(&bars->full[STAGES + sb]), pb, abort, p.err, 3)) { ok = false; break; }
+                            ptx::tc_fence_after();
+                            const uint32_t b0 = ptx::smem_u32(sB + sb * B_STRIDE);
+                            // column tap kx: the 128 output pixels read box rows kx .. kx + 127.
+                            // The 128B swizzle follows address bits, so a start 1-2 rows
+                            // into the atom needs no base-offset field.
+#pragma unroll
+                            for (int k = 0; k < ROW_BYTES / 32; ++k) {
+                                uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
+                                uint64_t ad = ptx::smem_desc(a0 + kx * ROW_BYTES + k * 32, ROW_BYTES);
+                                if (F8) ptx::mma_f8(d, ad, bd, IDESC, accumulate | (uint32_t)k);
+                                else ptx::mma_bf16(d, ad, bd, IDESC, accumulate | (uint32_t)k);
+                            }
+                            accumulate = 1;
+                            issued_any = true;
+                            ptx::mma_commit(ptx::smem_u32(&bars->empty[STAGES + sb]));
+                            if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
+                        }
+                        if (!ok) break;
+                        ptx::mma_commit(ptx::smem_u32(&bars->empty[sa]));
+                        if (++sa == STAGES) { sa = 0; pa ^= 1; }
+                    }
+                if (!ok) break;
+                ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
+                if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
+            }
+            if (*abort && issued_any) {
+                ptx::mma_commit(ptx::smem_u32(&bars->drain));
+                long long t0 = clock64();
+                while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->drain), 0) && clock64() - t0 < kWaitCycles) {}
+            }
+        } else if (lane == 0) {
             int stage = 0;
             uint32_t phase_bit = 0;
             int acc = 0;
@@ -301,15 +403,45 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 float nb[3][3][5];
                 const int h2 = p.gh, w2 = p.gw;
                 const float *fm = p.epi.fm_prev + (size_t)n * h2 * w2 * 5;
+                if (p.tw_log >= 5) {
+                    // a warp covers 32 consecutive pixels of one row: each lane loads its
+                    // own column (coalesced) and takes its neighbours' by shuffle
+                    const int xc = min(gx, w2 - 1);
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+                    for (int a = 0; a < 3; ++a) {
+                        const int yy = min(max(gy + a - 1, 0), h2 - 1);
+                        const float *src = fm + ((size_t)yy * w2 + xc) * 5;
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        int yy = min(max(gy + a - 1, 0), h2 - 1), xx = min(max(gx + b - 1, 0), w2 - 1);
-                        const float *src = fm + ((size_t)yy * w2 + xx) * 5;
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) nb[a][b][k] = valid ? __ldg(src + k) : 0.f;
+                        for (int k = 0; k < 5; ++k) nb[a][1][k] = __ldg(src + k);
                     }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            nb[a][0][k] = __shfl_up_sync(0xffffffffu, nb[a][1][k], 1);
+                            nb[a][2][k] = __shfl_down_sync(0xffffffffu, nb[a][1][k], 1);
+                        }
+                    if (lane == 0 || lane == 31) {
+                        const int b = lane == 0 ? 0 : 2;
+                        const int xx = lane == 0 ? max(xc - 1, 0) : min(xc + 1, w2 - 1);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const int yy = min(max(gy + a - 1, 0), h2 - 1);
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(fm + ((size_t)yy * w2 + xx) * 5 + k);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            int yy = min(max(gy + a - 1, 0), h2 - 1), xx = min(max(gx + b - 1, 0), w2 - 1);
+                            const float *src = fm + ((size_t)yy * w2 + xx) * 5;
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(src + k);
+                        }
+                }
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
                 ptx::tc_fence_after();
 #pragma unroll
@@ -543,6 +675,55 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, 
     return FVV_OK;
 }
 
+// Halo configurations (128-byte operand rows, one accumulator block): A boxes of
+// 130 rows and B slices in separate rings, sized per N tile by hand so that the
+// resident CTAs fill the shared-memory budget.
+template <int BN> struct HaloCfg {
+    static constexpr uint32_t A = (130 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
+    static constexpr uint32_t TMEM_COLS = AccCfg<BN, 1>::TMEM_COLS;
+    static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 ? 2 : 3);
+    static constexpr int STAGES = BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3));
+    static constexpr int STAGES_B = BN >= 256 ? 4 : (BN >= 128 ? 3 : 4);
+    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + sizeof(Bars) + 1024;
+    static_assert(CTAS * SMEM <= kSmemBudget + 8 * 1024 && CTAS * TMEM_COLS <= 512 && STAGES >= 2 && STAGES_B >= 2,
+                  "halo config");
+};
+
+template <int BN, int F8>
+int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+    using C = HaloCfg<BN>;
+    constexpr int CK = F8 ? 128 : 64;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, C::STAGES_B>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+bool halo_ok(int bn, bool f8) { return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256); }
+
+int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+    if (f8) return launch_halo<256, 1>(ma, mb, p, st);
+    switch (bn) {
+    case 32: return launch_halo<32, 0>(ma, mb, p, st);
+    case 64: return launch_halo<64, 0>(ma, mb, p, st);
+    case 128: return launch_halo<128, 0>(ma, mb, p, st);
+    default: return launch_halo<256, 0>(ma, mb, p, st);
+    }
+}
+
 int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p,
              cudaStream_t st) {
     if (f8) {
@@ -702,6 +883,11 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         int tw = force < pix_log ? force : pix_log;
         if (pix_log - tw <= 8) s = Shape{pix_log - tw, tw};
     }
+    // default tile of the 3x3 stride-1 layers with 128-byte operand rows: one row of
+    // 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
+    const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && ck * es == 128 && halo_ok(bn, f8) &&
+                      p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT);
+    if (halo) s = Shape{0, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
@@ -745,11 +931,12 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)tw_, (cuuint32_t)th_, 1};
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1};
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
     g_encode_u8 = false;
     FVV_TRY(rc);
+    if (halo) return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, p, st);
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, p, st);
 }
 

@@ -49,8 +49,10 @@ def test_fp8_requires_calibration(torch_cuda):
     assert e.value.code == fvv.FVV_EINVAL
 
 
+# (19, 42): 8 x 16 tiles; (3, 200): one-row halo tiles (130-pixel A boxes), ragged tail
+@pytest.mark.parametrize("h,ww", [(19, 42), (3, 200)])
 @pytest.mark.parametrize("name", ["vib1.m0", "vib2.m3", "vib0.m5"])
-def test_fp8_layer_matches_dequantised_oracle(torch_cuda, name):
+def test_fp8_layer_matches_dequantised_oracle(torch_cuda, name, h, ww):
     torch = torch_cuda
     H, W = 64, 96
     it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=3)
@@ -61,7 +63,7 @@ def test_fp8_layer_matches_dequantised_oracle(torch_cuda, name):
     w, b = weights.layer_views(blob())[name]
     wq_codes, wq = _e4m3(torch, w / s_w[:, None, None, None])
     rng = np.random.default_rng(li)
-    n, h, ww = 2, 19, 42
+    n = 2
     x = np.maximum(rng.standard_normal((n, h, ww, 256)), 0) * (100 * s_a)
     xq_codes, xq = _e4m3(torch, x / s_a)
     xd = torch.from_numpy(np.ascontiguousarray(xq_codes)).cuda()

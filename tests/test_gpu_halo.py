@@ -1,0 +1,96 @@
+"""GPU parity of the halo path of the tensor-core convolutions.
+
+3x3 stride-1 layers (and the all-phase transposed convs) with 128-byte operand
+rows run, on grids at least 96 pixels wide, on tiles of one 128-pixel row whose
+A operand is ONE box of 130 pixels per (row tap, channel block): the three
+column taps read it 0, 1, 2 rows in.  Checks:
+
+* each such layer alone on wide ragged grids (last tile partly outside the
+  grid, zero padding on both sides) against the oracle's conv of the same
+  bf16-rounded input and weights, the bar of the per-layer tests;
+* the whole BF16 forward with the halo tiles equals, bit for bit, the same
+  forward with every layer forced onto plain 1 x 128 tiles: both accumulate
+  the K loop in the order (row tap, channel block, column tap).
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2112_10603_b300 as fvv
+from synth import weights
+from tests.gpu_common import blob, pair
+
+pytestmark = pytest.mark.gpu
+
+HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    return torch
+
+
+def _bf16_round(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+@pytest.mark.parametrize("name", HALO_LAYERS)
+def test_halo_layer_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    names = [m[0] for m in weights.manifest()]
+    li = names.index(name)
+    _, kind, ci, co, stride, relu = weights.manifest()[li]
+    assert stride == 1 or kind == "convT"
+    rng = np.random.default_rng(300 + li)
+    # grid widths 260 = 2 x 128 + 4 (conv) and 131 = 128 + 3 (transposed conv input)
+    H, W = (3, 131) if kind == "convT" else (3, 260)
+    n = 2
+    cs = ci + (64 if li % 2 else 0)        # a wider pixel stride and a channel offset
+    coff = 64 if li % 2 else 0
+    x = np.zeros((n, H, W, cs), np.float32)
+    x[..., coff:coff + ci] = rng.standard_normal((n, H, W, ci)) * 0.5
+    x = _bf16_round(torch, x)
+    wv, bv = weights.layer_views(blob())[name]
+    wq = _bf16_round(torch, wv)
+    it = fvv.Interpolator(blob(), 64, 64, precision=fvv.FVV_BF16, max_views=1)
+    Ho, Wo = (2 * H, 2 * W) if kind == "convT" else (H, W)
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    out = torch.full((n, Ho, Wo, co + 3), -7.0, dtype=torch.float32, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, cs, coff, n, H, W, out, co + 3, 2, True)
+    fvv.fvv_interp_status(it.h)
+    got = out.cpu().numpy()
+    assert (got[..., :2] == -7).all() and (got[..., 2 + co:] == -7).all(), "wrote outside its channel slot"
+    for i in range(n):
+        xi = x[i, ..., coff:coff + ci]
+        if kind == "conv":
+            ref = oracle.conv3x3(xi, wq, bv, stride=1, relu=relu)
+        else:
+            ref = oracle.conv_transpose4x4(xi, wq, bv, relu=relu)
+        scale = max(1.0, float(np.abs(ref).max()))
+        err = np.abs(got[i, ..., 2:2 + co] - ref).max()
+        assert err <= 1e-4 * scale, (name, i, err, scale)
+
+
+def test_halo_network_bitwise_plain_tiles(torch_cuda, tmp_path):
+    torch = torch_cuda
+    # 64 x 512: VIB2's 256-channel convs, vib2.t1, ref.e1b and ref.d3 take halo tiles
+    H, W = 64, 512
+    left, right = pair(21, H, W, 10.0)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.3, 0.8]
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=2)
+    halo = it.run(L, R, ts).cpu().numpy()
+    # force every layer onto plain tiles 128 pixels wide through a tile cache entry
+    cache = tmp_path / "plain.json"
+    key = f"{H}x{W} n2 p{fvv.FVV_BF16}"
+    cache.write_text(json.dumps({key: {m[0]: 7 for m in weights.manifest()}}))
+    it.autotune(2, str(cache))
+    plain = it.run(L, R, ts).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    np.testing.assert_array_equal(halo, plain)
