@@ -187,22 +187,26 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
 // RefineNet's last layer (Conv2d 16 -> 3, then Sigmoid, Table 3) fused with the
 // residual output: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped.  Only
 // 3 output channels: a tensor-core tile would use 3 of its 16 columns, so this is
-// a shared-memory-tiled direct conv.  A block computes 32 x 8 output pixels of one
-// view from an (8 + 2) x (32 + 2) input patch (16 bf16 channels per pixel, stored
-// with a 9-word pitch so that neighbouring pixels fall in different banks).
-constexpr int OC_TX = 32, OC_TY = 8, OC_PITCH = 9; // words per pixel in shared memory
+// a shared-memory-tiled direct conv.  A block computes 32 x 32 output pixels of one
+// view from a (32 + 2) x (32 + 2) input patch (16 bf16 channels per pixel, stored
+// with a 9-word pitch so that neighbouring pixels fall in different banks).  Each
+// thread owns a column of 4 output rows: every input value it loads (6 rows x 3
+// columns per channel pair) feeds up to 3 of them, and each channel pair's 54
+// weights are loaded once for the 4 outputs.
+constexpr int OC_TX = 32, OC_TY = 8, OC_RPT = 4, OC_PITCH = 9; // OC_PITCH: words per pixel
+constexpr int OC_ROWS = OC_TY * OC_RPT;                          // output rows per block
 
 __global__ void __launch_bounds__(OC_TX *OC_TY)
 out_conv_fused_kernel(const bf16 *in, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
                       float *const *outp, int H, int W) {
-    __shared__ uint32_t tile[(OC_TY + 2) * (OC_TX + 2) * OC_PITCH];
-    __shared__ float ws[144 * 3];
+    __shared__ uint32_t tile[(OC_ROWS + 2) * (OC_TX + 2) * OC_PITCH];
+    __shared__ __align__(8) float ws[144 * 3];
     __shared__ float bs[3];
     const int tid = threadIdx.x, n = blockIdx.z;
-    const int x0 = blockIdx.x * OC_TX, y0 = blockIdx.y * OC_TY;
+    const int x0 = blockIdx.x * OC_TX, y0 = blockIdx.y * OC_ROWS;
     for (int i = tid; i < 144 * 3; i += blockDim.x) ws[i] = wp[i];
     if (tid < 3) bs[tid] = bias[tid];
-    const int npx = (OC_TY + 2) * (OC_TX + 2);
+    const int npx = (OC_ROWS + 2) * (OC_TX + 2);
     for (int i = tid; i < npx * 2; i += blockDim.x) {
         int p = i >> 1, half = i & 1;
         int iy = y0 - 1 + p / (OC_TX + 2), ix = x0 - 1 + p % (OC_TX + 2);
@@ -214,29 +218,53 @@ out_conv_fused_kernel(const bf16 *in, int Hp, int Wp, const float *wp, const flo
     }
     __syncthreads();
     const int tx = tid % OC_TX, ty = tid / OC_TX;
-    const int oy = y0 + ty, ox = x0 + tx;
-    if (oy >= H || ox >= W) return;
-    float acc[3] = {0.f, 0.f, 0.f};
+    const int ox = x0 + tx, oy0 = y0 + ty * OC_RPT;
+    if (ox >= W || oy0 >= H) return;
+    float acc[OC_RPT][3];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const uint32_t *px = tile + ((ty + tap / 3) * (OC_TX + 2) + tx + tap % 3) * OC_PITCH;
+    for (int j = 0; j < OC_RPT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
+    const uint32_t *col = tile + (ty * OC_RPT * (OC_TX + 2) + tx) * OC_PITCH;
+#pragma unroll 1
+    for (int c2 = 0; c2 < 8; ++c2) {
+        float w[9][6]; // tap -> (channel 2 c2: co 0..2, channel 2 c2 + 1: co 0..2)
 #pragma unroll
-        for (int c2 = 0; c2 < 8; ++c2) {
-            __nv_bfloat162 hv;
-            memcpy(&hv, px + c2, 4);
-            float2 v = __bfloat1622float2(hv);
-            const float *wr = ws + (tap * 16 + 2 * c2) * 3;
+        for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-            for (int co = 0; co < 3; ++co) acc[co] = fmaf(v.y, wr[3 + co], fmaf(v.x, wr[co], acc[co]));
-        }
+            for (int k = 0; k < 3; ++k) {
+                float2 f = *reinterpret_cast<const float2 *>(ws + (tap * 16 + 2 * c2) * 3 + 2 * k);
+                w[tap][2 * k] = f.x;
+                w[tap][2 * k + 1] = f.y;
+            }
+#pragma unroll
+        for (int r = 0; r < OC_RPT + 2; ++r)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                __nv_bfloat162 hv;
+                memcpy(&hv, col + (r * (OC_TX + 2) + dx) * OC_PITCH + c2, 4);
+                const float2 v = __bfloat1622float2(hv);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const int j = r - dy;
+                    if (j < 0 || j >= OC_RPT) continue;
+                    const float *wt = w[dy * 3 + dx];
+#pragma unroll
+                    for (int co = 0; co < 3; ++co) acc[j][co] = fmaf(v.y, wt[3 + co], fmaf(v.x, wt[co], acc[j][co]));
+                }
+            }
     }
-    const size_t q = ((size_t)n * Hp + oy) * Wp + ox;
-    float *out = *outp + (((size_t)n * H + oy) * W + ox) * 3;
+    float *out = *outp;
 #pragma unroll
-    for (int co = 0; co < 3; ++co) {
-        float z = acc[co] + bs[co];
-        float r = 2.f / (1.f + expf(-z)) - 1.f;
-        out[co] = fminf(fmaxf(__ldg(ib + q * 3 + co) + r, 0.f), 1.f);
+    for (int j = 0; j < OC_RPT; ++j) {
+        const int oy = oy0 + j;
+        if (oy >= H) break;
+        const size_t q = ((size_t)n * Hp + oy) * Wp + ox;
+        float *o = out + (((size_t)n * H + oy) * W + ox) * 3;
+#pragma unroll
+        for (int co = 0; co < 3; ++co) {
+            float z = acc[j][co] + bs[co];
+            float r = 2.f / (1.f + expf(-z)) - 1.f;
+            o[co] = fminf(fmaxf(__ldg(ib + q * 3 + co) + r, 0.f), 1.f);
+        }
     }
 }
 
@@ -244,7 +272,7 @@ out_conv_fused_kernel(const bf16 *in, int Hp, int Wp, const float *wp, const flo
 
 int launch_out_conv_fused(const bf16 *in, int N, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
                           float *const *outp, int H, int W, cudaStream_t st) {
-    dim3 grid(ceil_div(W, OC_TX), ceil_div(H, OC_TY), N);
+    dim3 grid(ceil_div(W, OC_TX), ceil_div(H, OC_ROWS), N);
     out_conv_fused_kernel<<<grid, OC_TX * OC_TY, 0, st>>>(in, Hp, Wp, wp, bias, ib, outp, H, W);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());

@@ -61,6 +61,7 @@ struct TcParams {
     int out_fp8;            // store E4M3 codes of value * out_q (saturating)
     float out_q;
     float *amax;            // calibration: running max |output| (NULL: off)
+    int tma_store;          // epilogue stages each warp's 32 rows in shared memory, TMA stores them
 };
 
 __device__ __forceinline__ uint8_t to_e4m3(float v) {
@@ -148,9 +149,11 @@ template <int BN, int MT> struct AccCfg {
 // 130 pixels per (row tap ky, channel block) serves the three column taps kx, whose
 // A operands start 0, 1, 2 rows into it; A boxes (STAGES ring) and B slices
 // (STAGES_B ring) are pipelined separately.  K order is (ky, block, kx) on both paths.
-template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES>
+// TS = 1: shared-memory staging for the TMA-store epilogue (used when p.tma_store).
+template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
-conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
     constexpr uint32_t A_BYTES = HALO ? 130 * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
@@ -164,7 +167,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_STRIDE;
-    Bars *bars = (Bars *)(sB + (HALO ? STAGES_B : STAGES) * B_STRIDE);
+    // epilogue staging: per epilogue warp two buffers of 32 rows x STG_ROW bytes
+    constexpr uint32_t STG_ROW = BN * 2 < 128 ? BN * 2 : 128, STG_BYTES = 32 * STG_ROW;
+    uint8_t *stg = sB + (HALO ? STAGES_B : STAGES) * B_STRIDE;
+    Bars *bars = (Bars *)(stg + (TS ? 8 * STG_BYTES : 0));
     volatile int *abort = &bars->abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -185,6 +191,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ptx::fence_proxy_async_smem();
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
+        if (TS && p.tma_store) ptx::prefetch_tmap(&tmC);
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), TMEM_COLS);
@@ -387,6 +394,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int row = q * 32 + lane;    // tile row = accumulator lane
         int acc = 0;
         uint32_t acc_phase = 0;
+        uint32_t scnt = 0;                // staged chunks of this warp (buffer = scnt & 1)
+        const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * 2 * STG_BYTES);
         const int tw = 1 << p.tw_log;
         const int dy = row >> p.tw_log, dx = row & (tw - 1);
         for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
@@ -488,6 +497,75 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
             ptx::tc_fence_after();
             const int ncols = p.mode == MODE_T3 ? 4 * p.co : p.co; // columns that hold outputs
+            if (TS && p.tma_store) {
+            // Each warp writes its 32 rows chunk by chunk (STG_ROW bytes of channels per
+            // row) into a swizzled staging buffer and one lane stores the box with TMA
+            // (rows outside the output are clipped by the tensor map).  bf16 or E4M3.
+            const int oes = p.out_fp8 ? 1 : 2;
+            const int chb = BN * oes < 128 ? BN * oes : 128, chn = chb / oes;
+            const uint32_t swm = chb == 128 ? 7u : (chb == 64 ? 3u : 1u);
+#pragma unroll 1
+            for (int m = 0; m < MT; ++m) {
+                const int rb = m * 128 + q * 32, rm = rb + lane;
+                const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
+                const bool valid = gy < p.gh && gx < p.gw;
+                const int by = y0 + (rb >> p.tw_log), bx = x0 + (rb & (tw - 1));
+                const uint32_t tb = tbase + m * BN;
+#pragma unroll 1
+                for (int k0 = 0; k0 < BN; k0 += chn) {
+                    // the buffer staged two chunks ago must have been read by its store
+                    if (lane == 0) ptx::bulk_wait_read<1>();
+                    __syncwarp();
+                    const uint32_t sbuf = stg_warp + (scnt & 1) * STG_BYTES;
+#pragma unroll 1
+                    for (int c = k0; c < k0 + chn; c += 16) {
+                        uint32_t r[16];
+                        __syncwarp();
+                        ptx::tmem_ld16(tb + c, r);
+                        ptx::tmem_ld_wait();
+                        float v[16];
+                        float vmax = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float sc = p.acc_scale ? __ldg(p.acc_scale + c + j) : 1.f;
+                            float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + c + j);
+                            v[j] = p.relu ? fmaxf(a, 0.f) : a;
+                            vmax = fmaxf(vmax, fabsf(v[j]));
+                        }
+                        if (p.amax && valid) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
+                        const uint32_t a0 = sbuf + lane * chb + (c - k0) * oes;
+                        if (p.out_fp8) {
+                            uint8_t q8[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) q8[j] = to_e4m3(v[j] * p.out_q);
+                            uint4 w;
+                            memcpy(&w, q8, 16);
+                            ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), w);
+                        } else {
+                            __nv_bfloat162 h[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            uint4 w0, w1;
+                            memcpy(&w0, &h[0], 16);
+                            memcpy(&w1, &h[4], 16);
+                            const uint32_t a1 = a0 + 16;
+                            ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), w0);
+                            ptx::st_shared_v4(a1 ^ (((a1 >> 7) & swm) << 4), w1);
+                        }
+                    }
+                    ptx::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (p.mode == MODE_T)
+                            ptx::tma_store_5d(&tmC, sbuf, (ph & 1) * p.out_cs + p.out_coff + k0, bx, ph >> 1, by, n);
+                        else
+                            ptx::tma_store_4d(&tmC, sbuf, p.out_coff + k0, bx, by, n);
+                        ptx::bulk_commit();
+                    }
+                    ++scnt;
+                }
+            }
+            } else {
 #pragma unroll 1
             for (int m = 0; m < MT; ++m) {
             // row block m of the tile: accumulator m, pixel rows m * 128 + lane row
@@ -556,10 +634,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             }
             }
+            }
             ptx::tc_fence_before();
             ptx::mbar_arrive(ptx::smem_u32(&bars->tmem_empty[acc]));
             if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
         }
+        // every TMA store of this warp has finished before shared memory goes away
+        if (TS && lane == 0) ptx::bulk_wait<0>();
     }
 
     ptx::tc_fence_before();
@@ -638,25 +719,29 @@ int mt_for(int bn, int ck) { return ck == 64 && bn == 128 ? 2 : 1; }
 // configs put several CTAs on an SM (their TMEM columns and shared memory allow
 // it), so more TMA copies are in flight per SM: those layers are bound by copy latency.
 constexpr uint32_t kSmemBudget = 220 * 1024; // per SM, for all resident CTAs
-template <int BN, int CK, int MT, int F8 = 0> struct Cfg {
+// TS = 1 adds the epilogue's staging buffers (4 warps x 2 x 32 rows).
+constexpr uint32_t stg_bytes(int bn, int ts) { return ts ? 8u * 32u * (bn * 2 < 128 ? bn * 2 : 128) : 0u; }
+template <int BN, int CK, int MT, int F8 = 0, int TS = 0> struct Cfg {
     static constexpr uint32_t ES = F8 ? 1 : 2;
     static constexpr uint32_t A = ((128 * MT * CK * ES) + 1023) & ~1023u, B = ((BN * CK * ES) + 1023) & ~1023u;
+    static constexpr uint32_t STG = stg_bytes(BN, TS);
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
-    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048) / (A + B)); }
-    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
+    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / (A + B)); }
+    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 3 + !TS ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for((512 / TMEM_COLS) < 4 ? (512 / TMEM_COLS) : 4);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * (A + B) + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * (A + B) + STG + sizeof(Bars) + 1024;
     static_assert(STAGES >= 2 && CTAS * TMEM_COLS <= 512, "tensor-core config");
 };
 
 int g_num_sms = 0;
 
-template <int BN, int CK, int F8 = 0>
-int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
+template <int BN, int CK, int F8, int TS>
+int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+               cudaStream_t st) {
     constexpr int MT = (!F8 && CK == 64 && BN == 128) ? 2 : 1; // = mt_for(BN, CK)
-    using C = Cfg<BN, CK, MT, F8>;
-    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8>;
+    using C = Cfg<BN, CK, MT, F8, TS>;
+    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8, 0, C::STAGES, TS>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -669,7 +754,7 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, 
     }
     int slots = g_num_sms * C::CTAS;
     int grid = p.num_tiles < slots ? p.num_tiles : slots;
-    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, p);
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());
     return FVV_OK;
@@ -678,22 +763,26 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, 
 // Halo configurations (128-byte operand rows, one accumulator block): A boxes of
 // 130 rows and B slices in separate rings, sized per N tile by hand so that the
 // resident CTAs fill the shared-memory budget.
-template <int BN> struct HaloCfg {
+template <int BN, int TS> struct HaloCfg {
     static constexpr uint32_t A = (130 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
+    static constexpr uint32_t STG = stg_bytes(BN, TS);
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, 1>::TMEM_COLS;
-    static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 ? 2 : 3);
-    static constexpr int STAGES = BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3));
-    static constexpr int STAGES_B = BN >= 256 ? 4 : (BN >= 128 ? 3 : 4);
-    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + sizeof(Bars) + 1024;
+    static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 || TS ? 2 : 3);
+    static constexpr int STAGES = TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
+                                     : (BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
+    static constexpr int STAGES_B = TS ? (BN >= 256 ? 3 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
+                                       : (BN >= 256 ? 4 : (BN >= 128 ? 3 : 4));
+    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
     static_assert(CTAS * SMEM <= kSmemBudget + 8 * 1024 && CTAS * TMEM_COLS <= 512 && STAGES >= 2 && STAGES_B >= 2,
                   "halo config");
 };
 
-template <int BN, int F8>
-int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
-    using C = HaloCfg<BN>;
+template <int BN, int F8, int TS>
+int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+                cudaStream_t st) {
+    using C = HaloCfg<BN, TS>;
     constexpr int CK = F8 ? 128 : 64;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, C::STAGES_B>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, C::STAGES_B, TS>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -706,7 +795,7 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p,
     }
     int slots = g_num_sms * C::CTAS;
     int grid = p.num_tiles < slots ? p.num_tiles : slots;
-    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, p);
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());
     return FVV_OK;
@@ -714,31 +803,44 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p,
 
 bool halo_ok(int bn, bool f8) { return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256); }
 
-int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p, cudaStream_t st) {
-    if (f8) return launch_halo<256, 1>(ma, mb, p, st);
+template <int TS>
+int dispatch_halo_ts(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
+                     const TcParams &p, cudaStream_t st) {
+    if (f8) return launch_halo<256, 1, TS>(ma, mb, mc, p, st);
     switch (bn) {
-    case 32: return launch_halo<32, 0>(ma, mb, p, st);
-    case 64: return launch_halo<64, 0>(ma, mb, p, st);
-    case 128: return launch_halo<128, 0>(ma, mb, p, st);
-    default: return launch_halo<256, 0>(ma, mb, p, st);
+    case 32: return launch_halo<32, 0, TS>(ma, mb, mc, p, st);
+    case 64: return launch_halo<64, 0, TS>(ma, mb, mc, p, st);
+    case 128: return launch_halo<128, 0, TS>(ma, mb, mc, p, st);
+    default: return launch_halo<256, 0, TS>(ma, mb, mc, p, st);
     }
 }
 
-int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const TcParams &p,
-             cudaStream_t st) {
+int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
+                  const TcParams &p, cudaStream_t st) {
+    return p.tma_store ? dispatch_halo_ts<1>(bn, f8, ma, mb, mc, p, st) : dispatch_halo_ts<0>(bn, f8, ma, mb, mc, p, st);
+}
+
+template <int TS>
+int dispatch_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
+                const TcParams &p, cudaStream_t st) {
     if (f8) {
-        if (bn == 256 && ck == 128) return launch_cfg<256, 128, 1>(ma, mb, p, st);
+        if (bn == 256 && ck == 128) return launch_cfg<256, 128, 1, TS>(ma, mb, mc, p, st);
         set_error("no FP8 tensor-core kernel for N=%d, CK=%d", bn, ck);
         return FVV_EINVAL;
     }
 #define FVV_CASE(BN_, CK_) \
-    if (bn == BN_ && ck == CK_) return launch_cfg<BN_, CK_>(ma, mb, p, st);
+    if (bn == BN_ && ck == CK_) return launch_cfg<BN_, CK_, 0, TS>(ma, mb, mc, p, st);
     FVV_CASE(16, 16) FVV_CASE(16, 64) FVV_CASE(32, 16) FVV_CASE(32, 32) FVV_CASE(32, 64)
     FVV_CASE(64, 32) FVV_CASE(64, 64) FVV_CASE(128, 16) FVV_CASE(128, 32) FVV_CASE(128, 64)
     FVV_CASE(256, 64)
 #undef FVV_CASE
     set_error("no tensor-core kernel for N=%d, CK=%d", bn, ck);
     return FVV_EINVAL;
+}
+
+int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
+             const TcParams &p, cudaStream_t st) {
+    return p.tma_store ? dispatch_ts<1>(bn, ck, f8, ma, mb, mc, p, st) : dispatch_ts<0>(bn, ck, f8, ma, mb, mc, p, st);
 }
 
 } // namespace
@@ -936,8 +1038,38 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     }
     g_encode_u8 = false;
     FVV_TRY(rc);
-    if (halo) return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, p, st);
-    return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, p, st);
+    // TMA-store epilogue: plain bf16 / E4M3 stores of whole 16-byte channel groups
+    // (every output channel of the tile is a real channel: C_out = N tile)
+    CUtensorMap mc = ma;
+    {
+        const int oes = p.out_fp8 ? 1 : 2, chb = bn * oes < 128 ? bn * oes : 128;
+        p.tma_store = (!epi || epi->mode == EPI_STORE) && !out_f32 && p.mode != MODE_T3 && L.co == bn &&
+                      (chb == 32 || chb == 64 || chb == 128) && (out_cs * oes) % 16 == 0 &&
+                      (out_coff * oes) % 16 == 0 && ((uintptr_t)out % 16) == 0;
+        if (p.tma_store) {
+            const cuuint64_t oe = (cuuint64_t)oes;
+            const cuuint32_t bw = tw_ < 32 ? tw_ : 32, bh = 32 / bw;
+            g_encode_u8 = p.out_fp8 != 0;
+            if (p.mode == MODE_T) {
+                cuuint64_t dims[5] = {(cuuint64_t)2 * out_cs, (cuuint64_t)p.gw, 2, (cuuint64_t)p.gh, (cuuint64_t)N};
+                cuuint64_t strides[4] = {(cuuint64_t)2 * out_cs * oe, (cuuint64_t)p.out_w * out_cs * oe,
+                                         (cuuint64_t)2 * p.out_w * out_cs * oe,
+                                         (cuuint64_t)p.out_h * p.out_w * out_cs * oe};
+                cuuint32_t box[5] = {(cuuint32_t)(chb / oes), bw, 1, bh, 1};
+                rc = encode(&mc, 5, out, dims, strides, box, chb);
+            } else {
+                cuuint64_t dims[4] = {(cuuint64_t)out_cs, (cuuint64_t)p.out_w, (cuuint64_t)p.out_h, (cuuint64_t)N};
+                cuuint64_t strides[3] = {(cuuint64_t)out_cs * oe, (cuuint64_t)p.out_w * out_cs * oe,
+                                         (cuuint64_t)p.out_h * p.out_w * out_cs * oe};
+                cuuint32_t box[4] = {(cuuint32_t)(chb / oes), bw, bh, 1};
+                rc = encode(&mc, 4, out, dims, strides, box, chb);
+            }
+            g_encode_u8 = false;
+            FVV_TRY(rc);
+        }
+    }
+    if (halo) return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
+    return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
 }
 
 } // namespace fvv

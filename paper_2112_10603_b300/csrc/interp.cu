@@ -158,7 +158,7 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     if (!h->skip_cams) {
         int hh = Hp, ww = Wp;
         const void *cur = h->img0; // FP32 frame: the 3-channel first layer runs on the SIMT kernel
-        int cur_cs = 3;
+        int cur_cs = 4;
         const int C[4] = {16, 32, 64, 128};
         for (int k = 0; k < 4; ++k) {
             FVV_TRY(conv(h, kCtx + 2 * k, cur, cur_cs, 0, n_cams, hh, ww, h->ctxt, C[k], 0, false, st));
@@ -171,10 +171,12 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     for (int s = 0; s < 3; ++s) {
         int hs = Hp >> (2 - s), ws = Wp >> (2 - s);
         int cx = s == 0 ? cx0 : cx1;
-        if (s == 0) FVV_TRY(launch_vib0_input<T>(h->img2, vt, nv, hs, ws, xb, cx, st));
-        else FVV_TRY(launch_stage_input<T>(s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, xb, cx, st));
+        // VIB0's input has its own buffer: each layout keeps its zero padding channels
+        T *x = s == 0 ? (T *)h->xb0 : xb;
+        if (s == 0) FVV_TRY(launch_vib0_input<T>(h->img2, vt, nv, hs, ws, x, cx, st));
+        else FVV_TRY(launch_stage_input<T>(s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, x, cx, st));
         int base = s * 10;
-        FVV_TRY(conv(h, base + 0, xb, cx, 0, nv, hs, ws, ta, 128, 0, false, st));
+        FVV_TRY(conv(h, base + 0, x, cx, 0, nv, hs, ws, ta, 128, 0, false, st));
         FVV_TRY(conv(h, base + 1, ta, 128, 0, nv, hs / 2, ws / 2, ma, 256, 0, false, st));
         T *src = ma, *dst = mb;
         for (int k = 0; k < 6; ++k) {
@@ -278,14 +280,18 @@ static int create_impl(fvv_interp *h, const float *blob) {
     }
     if (b16) FVV_TRY(tc_prepare(h, blob));
     // per-camera
-    FVV_TRY(dalloc_t(h, &h->img0, C * P * 3 * 4));
-    FVV_TRY(dalloc_t(h, &h->img1, C * P / 4 * 3 * 4));
-    FVV_TRY(dalloc_t(h, &h->img2, C * P / 16 * 3 * 4));
+    FVV_TRY(dalloc_t(h, &h->img0, C * P * 16));
+    FVV_TRY(dalloc_t(h, &h->img1, C * P / 4 * 16));
+    FVV_TRY(dalloc_t(h, &h->img2, C * P / 16 * 16));
     const int ctxC[4] = {16, 32, 64, 128};
     for (int k = 0; k < 4; ++k) FVV_TRY(dalloc(h, &h->ctx[k], C * (P >> (2 * k + 2)) * ctxC[k] * es));
     FVV_TRY(dalloc(h, &h->ctxt, C * (P / 4) * 16 * es));
     // per-view
     FVV_TRY(dalloc(h, &h->xb, V * P * (b16 ? 32 : 18) * es));
+    FVV_TRY(dalloc(h, &h->xb0, V * (P / 16) * (b16 ? 16 : 7) * es));
+    // bf16 stage inputs: their padding channels are never written, so clear once
+    FVV_CHECK_CUDA(cudaMemset(h->xb, 0, V * P * (b16 ? 32 : 18) * es));
+    FVV_CHECK_CUDA(cudaMemset(h->xb0, 0, V * (P / 16) * (b16 ? 16 : 7) * es));
     FVV_TRY(dalloc(h, &h->ta, V * P * 32 * es));
     FVV_TRY(dalloc(h, &h->ma, V * P * 16 * es));
     FVV_TRY(dalloc(h, &h->mb, V * P * 16 * es));
@@ -295,6 +301,7 @@ static int create_impl(fvv_interp *h, const float *blob) {
     FVV_TRY(dalloc_t(h, &h->z, V * P * 3 * 4));
     const int ucs[5] = {b16 ? 16 : 6, 96, 192, 384, 512};
     for (int k = 0; k < 5; ++k) FVV_TRY(dalloc(h, &h->u[k], V * (P >> (2 * k)) * ucs[k] * es));
+    FVV_CHECK_CUDA(cudaMemset(h->u[0], 0, V * P * ucs[0] * es));
     // the U-Net level tensors must start as zeros only where nothing writes: every
     // slot is written each run, so no clearing is needed.
     FVV_TRY(dalloc_t(h, &h->d_cam_l, V * 4));

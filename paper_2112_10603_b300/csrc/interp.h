@@ -49,10 +49,10 @@ struct fvv_interp {
     size_t w_off[fvv::kNumLayers] = {}, b_off[fvv::kNumLayers] = {};
     fvv::TcWeights tc[fvv::kNumLayers];
     // per-camera buffers
-    float *img0 = nullptr, *img1 = nullptr, *img2 = nullptr;
+    float4 *img0 = nullptr, *img1 = nullptr, *img2 = nullptr; // (R, G, B, 0) per pixel
     void *ctx[4] = {}, *ctxt = nullptr;
     // per-view buffers
-    void *xb = nullptr, *ta = nullptr, *ma = nullptr, *mb = nullptr;
+    void *xb = nullptr, *xb0 = nullptr, *ta = nullptr, *ma = nullptr, *mb = nullptr;
     float *fm[3] = {}, *ib = nullptr, *fk[4] = {}, *z = nullptr;
     void *u[5] = {};
     // view table and camera pointer table (device) + pinned host staging

@@ -21,16 +21,20 @@ int launch_out_conv_fused(const bf16 *in, int N, int Hp, int Wp, const float *wp
                           float *const *outp, int H, int W, cudaStream_t st);
 void pack_simt(int kind, int Ci, int Co, const float *w, float *dst);
 
-int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float *img0,
-                     float *img1, float *img2, cudaStream_t st);
+// Frame pyramid levels (img0 = padded frame, img1 = 1/2, img2 = 1/4 box levels):
+// one float4 (R, G, B, 0) per pixel.  bf16 stage inputs (x, u0) are written only
+// up to the last 8-channel group holding data; the padding channels above are
+// zeros from the allocation-time clear.
+int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float4 *img0,
+                     float4 *img1, float4 *img2, cudaStream_t st);
 template <typename T>
-int launch_vib0_input(const float *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st);
+int launch_vib0_input(const float4 *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st);
 template <typename T>
-int launch_stage_input(const float *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w, int circ,
+int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w, int circ,
                        T *x, int cs, cudaStream_t st);
 int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ, cudaStream_t st);
 template <typename T>
-int launch_final_blend(const float *img0, const float *FM, const ViewTab &vt, int nv, int h, int w, int circ,
+int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, int nv, int h, int w, int circ,
                        T *u0, int cs, float *ib, cudaStream_t st);
 template <typename T>
 int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, const ViewTab &vt, int nv,

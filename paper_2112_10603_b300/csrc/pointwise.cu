@@ -24,14 +24,16 @@ template <typename T> __device__ __forceinline__ T to_store(float v);
 template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 to_store<bf16>(float v) { return __float2bfloat16_rn(v); }
 
-// Store the N values of one pixel, zero-padded to cs channels.  The bf16
+// Store the N values of one pixel.  FP32 layouts are dense (cs = N).  The bf16
 // layouts keep cs a multiple of 8 so that every pixel is 16-byte aligned and is
-// written with 16-byte stores.
+// written with 16-byte stores; only the first round_up(N, 8) channels are written:
+// the channels above stay at the zeros the buffer was cleared to when allocated.
 template <int N> __device__ __forceinline__ void store_px(float *dst, const float (&v)[N], int cs) {
     for (int c = 0; c < cs; ++c) dst[c] = c < N ? v[c] : 0.f;
 }
-template <int N> __device__ __forceinline__ void store_px(bf16 *dst, const float (&v)[N], int cs) {
-    for (int c0 = 0; c0 < cs; c0 += 8) {
+template <int N> __device__ __forceinline__ void store_px(bf16 *dst, const float (&v)[N], int) {
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 8) {
         __nv_bfloat162 h[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -44,11 +46,23 @@ template <int N> __device__ __forceinline__ void store_px(bf16 *dst, const float
     }
 }
 
+// Frame pyramid levels hold one float4 (R, G, B, 0) per pixel: one 16-byte load per
+// bilinear tap.  Same arithmetic, channel by channel, as bilerp().
+__device__ __forceinline__ float3 bilerp_rgb(const float4 *img, const Taps &t) {
+    float4 a = __ldg(img + t.o00), b = __ldg(img + t.o01), d = __ldg(img + t.o10), e = __ldg(img + t.o11);
+    const float wx0 = 1.f - t.lx, wy0 = 1.f - t.ly;
+    float3 r;
+    r.x = wy0 * (wx0 * a.x + t.lx * b.x) + t.ly * (wx0 * d.x + t.lx * e.x);
+    r.y = wy0 * (wx0 * a.y + t.lx * b.y) + t.ly * (wx0 * d.y + t.lx * e.y);
+    r.z = wy0 * (wx0 * a.z + t.lx * b.z) + t.ly * (wx0 * d.z + t.lx * e.z);
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // a0: zero-pad each camera frame to Hp x Wp and build its 1/2 box level.
 // One thread per 2x2 block (= one pixel of the 1/2 level).
 __global__ void prep_cams_kernel(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp,
-                                 float *img0, float *img1) {
+                                 float4 *img0, float4 *img1) {
     int h2 = Hp / 2, w2 = Wp / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n_cams * h2 * w2) return;
@@ -69,50 +83,48 @@ __global__ void prep_cams_kernel(const float *const *cams, int n_cams, int H, in
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) v[3 * dx + ch] = in ? __ldg(src + ((size_t)y * W + x) * 3 + ch) : 0.f;
         }
-        float *d = img0 + ((size_t)c * P0 + (size_t)y * Wp + 2 * x2) * 3;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) d[k] = v[k];
+        float4 *d = img0 + (size_t)c * P0 + (size_t)y * Wp + 2 * x2;
+        d[0] = make_float4(v[0], v[1], v[2], 0.f);
+        d[1] = make_float4(v[3], v[4], v[5], 0.f);
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) s[ch] += v[ch] + v[3 + ch];
     }
-    float *d1 = img1 + ((size_t)c * (P0 / 4) + (size_t)y2 * w2 + x2) * 3;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) d1[ch] = s[ch] * 0.25f;
+    img1[(size_t)c * (P0 / 4) + (size_t)y2 * w2 + x2] = make_float4(s[0] * 0.25f, s[1] * 0.25f, s[2] * 0.25f, 0.f);
 }
 
 // a0: the 1/4 level as the 2x2 box average of the 1/2 level (= the 4x4 box).
-__global__ void box_quarter_kernel(const float *img1, int n_cams, int h2, int w2, float *img2) {
+__global__ void box_quarter_kernel(const float4 *img1, int n_cams, int h2, int w2, float4 *img2) {
     int h4 = h2 / 2, w4 = w2 / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n_cams * h4 * w4) return;
     int x = idx % w4;
     long long r = idx / w4;
     int y = r % h4, c = r / h4;
-    const float *s = img1 + (size_t)c * h2 * w2 * 3;
-    size_t p00 = ((size_t)(2 * y) * w2 + 2 * x) * 3, p10 = p00 + (size_t)w2 * 3;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-        img2[(size_t)idx * 3 + ch] = (s[p00 + ch] + s[p00 + 3 + ch] + s[p10 + ch] + s[p10 + 3 + ch]) * 0.25f;
+    const float4 *s = img1 + (size_t)c * h2 * w2;
+    size_t p00 = (size_t)(2 * y) * w2 + 2 * x, p10 = p00 + w2;
+    float4 a = s[p00], b = s[p00 + 1], d = s[p10], e = s[p10 + 1];
+    img2[idx] = make_float4((a.x + b.x + d.x + e.x) * 0.25f, (a.y + b.y + d.y + e.y) * 0.25f,
+                            (a.z + b.z + d.z + e.z) * 0.25f, 0.f);
 }
 
 // a2 input: [I_l/4, I_r/4, t] (7 channels, zero-padded to cs).
 template <typename T>
-__global__ void vib0_input_kernel(const float *img2, const ViewTab vt, int nv, int h, int w, T *x, int cs) {
+__global__ void vib0_input_kernel(const float4 *img2, const ViewTab vt, int nv, int h, int w, T *x, int cs) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)h * w;
     if (idx >= (long long)nv * P) return;
     int v = idx / P;
     long long p = idx % P;
-    const float *L = img2 + ((size_t)vt.cam_l[v] * P + p) * 3;
-    const float *R = img2 + ((size_t)vt.cam_r[v] * P + p) * 3;
-    float vals[7] = {L[0], L[1], L[2], R[0], R[1], R[2], vt.t[v]};
+    const float4 L = __ldg(img2 + (size_t)vt.cam_l[v] * P + p);
+    const float4 R = __ldg(img2 + (size_t)vt.cam_r[v] * P + p);
+    float vals[7] = {L.x, L.y, L.z, R.x, R.y, R.z, vt.t[v]};
     store_px(x + (size_t)idx * cs, vals, cs);
 }
 
 // a3: stage s input [I_l, I_r, W_l, W_r, M_up, F_up(4), t] (18 ch, zero-padded to cs)
 // at the stage grid h x w, from the previous stage's flow/mask FMp (h/2 x w/2 x 5).
 template <typename T>
-__global__ void stage_input_kernel(const float *imgs, const float *FMp, const ViewTab vt, int nv,
+__global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *x, int cs) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)h * w;
@@ -127,18 +139,13 @@ __global__ void stage_input_kernel(const float *imgs, const float *FMp, const Vi
     for (int c = 0; c < 5; ++c) up[c] = bilerp(fm, 5, c, u);
 #pragma unroll
     for (int c = 0; c < 4; ++c) up[c] *= 2.f;
-    const float *L = imgs + (size_t)vt.cam_l[v] * P * 3;
-    const float *R = imgs + (size_t)vt.cam_r[v] * P * 3;
+    const float4 *L = imgs + (size_t)vt.cam_l[v] * P;
+    const float4 *R = imgs + (size_t)vt.cam_r[v] * P;
     Taps tl = warp_taps(X, Y, up[0], up[1], h, w, circ);
     Taps tr = warp_taps(X, Y, up[2], up[3], h, w, circ);
-    float vals[18];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        vals[c] = L[(size_t)p * 3 + c];
-        vals[3 + c] = R[(size_t)p * 3 + c];
-        vals[6 + c] = bilerp(L, 3, c, tl);
-        vals[9 + c] = bilerp(R, 3, c, tr);
-    }
+    const float4 lc = __ldg(L + p), rc = __ldg(R + p);
+    const float3 wl = bilerp_rgb(L, tl), wr = bilerp_rgb(R, tr);
+    float vals[18] = {lc.x, lc.y, lc.z, rc.x, rc.y, rc.z, wl.x, wl.y, wl.z, wr.x, wr.y, wr.z};
     vals[12] = up[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) vals[13 + c] = up[c];
@@ -164,7 +171,7 @@ __global__ void residual_kernel(const float *FMp, float *res, int nv, int h, int
 // a5 (Eq. 1): I_l->m, I_r->m by the final flows, M = sigmoid(logit), blend.
 // Writes the refinement input [I_l->m, I_r->m] (zero-padded to cs) and I_blend.
 template <typename T>
-__global__ void final_blend_kernel(const float *img0, const float *FM, const ViewTab vt, int nv,
+__global__ void final_blend_kernel(const float4 *img0, const float *FM, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *u0, int cs, float *ib) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)h * w;
@@ -173,19 +180,17 @@ __global__ void final_blend_kernel(const float *img0, const float *FM, const Vie
     int p = idx % P;
     int X = p % w, Y = p / w;
     const float *f = FM + (size_t)idx * 5;
-    const float *L = img0 + (size_t)vt.cam_l[v] * P * 3;
-    const float *R = img0 + (size_t)vt.cam_r[v] * P * 3;
+    const float4 *L = img0 + (size_t)vt.cam_l[v] * P;
+    const float4 *R = img0 + (size_t)vt.cam_r[v] * P;
     Taps tl = warp_taps(X, Y, f[0], f[1], h, w, circ);
     Taps tr = warp_taps(X, Y, f[2], f[3], h, w, circ);
     float M = sigmoidf_(f[4]);
-    float vals[6];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float a = bilerp(L, 3, c, tl), b = bilerp(R, 3, c, tr);
-        vals[c] = a;
-        vals[3 + c] = b;
-        ib[(size_t)idx * 3 + c] = M * a + (1.f - M) * b;
-    }
+    const float3 a = bilerp_rgb(L, tl), b = bilerp_rgb(R, tr);
+    float vals[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
+    float *o = ib + (size_t)idx * 3;
+    o[0] = M * a.x + (1.f - M) * b.x;
+    o[1] = M * a.y + (1.f - M) * b.y;
+    o[2] = M * a.z + (1.f - M) * b.z;
     store_px(u0 + (size_t)idx * cs, vals, cs);
 }
 
@@ -293,8 +298,8 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 #define FVV_LAUNCH_CHECK() \
     do { count_launch(); FVV_CHECK_CUDA(cudaGetLastError()); } while (0)
 
-int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float *img0,
-                     float *img1, float *img2, cudaStream_t st) {
+int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float4 *img0,
+                     float4 *img1, float4 *img2, cudaStream_t st) {
     long long n = (long long)n_cams * (Hp / 2) * (Wp / 2);
     prep_cams_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cams, n_cams, H, W, Hp, Wp, img0, img1);
     FVV_LAUNCH_CHECK();
@@ -305,7 +310,7 @@ int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp,
 }
 
 template <typename T>
-int launch_vib0_input(const float *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st) {
+int launch_vib0_input(const float4 *img2, const ViewTab &vt, int nv, int h, int w, T *x, int cs, cudaStream_t st) {
     long long n = (long long)nv * h * w;
     vib0_input_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(img2, vt, nv, h, w, x, cs);
     FVV_LAUNCH_CHECK();
@@ -313,7 +318,7 @@ int launch_vib0_input(const float *img2, const ViewTab &vt, int nv, int h, int w
 }
 
 template <typename T>
-int launch_stage_input(const float *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w,
+int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *x, int cs, cudaStream_t st) {
     long long n = (long long)nv * h * w;
     stage_input_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, circ, x, cs);
@@ -329,7 +334,7 @@ int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ
 }
 
 template <typename T>
-int launch_final_blend(const float *img0, const float *FM, const ViewTab &vt, int nv, int h, int w,
+int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *u0, int cs, float *ib, cudaStream_t st) {
     long long n = (long long)nv * h * w;
     final_blend_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(img0, FM, vt, nv, h, w, circ, u0, cs, ib);
@@ -356,10 +361,10 @@ int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int
 }
 
 #define INST(T)                                                                                          \
-    template int launch_vib0_input<T>(const float *, const ViewTab &, int, int, int, T *, int, cudaStream_t); \
-    template int launch_stage_input<T>(const float *, const float *, const ViewTab &, int, int, int, int, T *, \
+    template int launch_vib0_input<T>(const float4 *, const ViewTab &, int, int, int, T *, int, cudaStream_t); \
+    template int launch_stage_input<T>(const float4 *, const float *, const ViewTab &, int, int, int, int, T *, \
                                        int, cudaStream_t);                                              \
-    template int launch_final_blend<T>(const float *, const float *, const ViewTab &, int, int, int, int, T *, \
+    template int launch_final_blend<T>(const float4 *, const float *, const ViewTab &, int, int, int, int, T *, \
                                        int, float *, cudaStream_t);                                     \
     template int launch_ctx_warp<T>(const float *, int, float *, const T *, int, const ViewTab &, int, int, int, \
                                     int, T *, int, int, int, cudaStream_t);
