@@ -145,20 +145,28 @@ template <int BN, int MT> struct AccCfg {
 
 // F8 = 1: E4M3 operands (kind::f8f6f4, K = 32 per MMA), else BF16 (kind::f16, K = 16);
 // either way one MMA consumes 32 bytes of every operand row.
-// HALO = 1 (stride-1 3x3 taps, 1 x 128-pixel tiles, 128-byte rows): one TMA box of
-// 130 pixels per (row tap ky, channel block) serves the three column taps kx, whose
-// A operands start 0, 1, 2 rows into it; A boxes (STAGES ring) and B slices
-// (STAGES_B ring) are pipelined separately.  K order is (ky, block, kx) on both paths.
+// HALO = 1 (stride-1 3x3 taps, MT x 128-pixel tiles, 128-byte rows): one TMA box of
+// MT image rows x 130 pixels per (row tap ky, channel block) serves the three column
+// taps kx, whose A operands start 0, 1, 2 rows into each 130-row block; A boxes
+// (STAGES ring) and B slices (STAGES_B ring) are pipelined separately.  K order is
+// (ky, block, kx) on both paths.  With MT = 2 each weight slice feeds two MMAs.
 // TS = 1: shared-memory staging for the TMA-store epilogue (used when p.tma_store).
-template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0>
+// MC = 1 (halo only): clusters of 2 CTAs on neighbouring tiles share every weight
+// slice: each CTA loads one half of its N rows and multicasts it into both CTAs'
+// rings, halving the weight traffic from L2.  A slot of the B ring is released by
+// both CTAs' MMA commits; tiles go in pairs (a pair's odd last member is computed
+// on a clamped tile and not stored).
+template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
+          int MC = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = HALO ? 130 * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
+    constexpr uint32_t A_BYTES = HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
-    static_assert(!HALO || (ROW_BYTES == 128 && MT == 1 && STAGES + STAGES_B <= 16), "halo config");
+    static_assert(!HALO || (ROW_BYTES == 128 && STAGES + STAGES_B <= 16), "halo config");
+    static_assert(!MC || HALO, "weight multicast runs on the halo path");
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -179,7 +187,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // halo: full/empty[0, STAGES) = A ring, [STAGES, STAGES + STAGES_B) = B ring
         for (int s = 0; s < (HALO ? STAGES + STAGES_B : STAGES); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), MC && s >= STAGES ? 2 : 1);
         }
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(ptx::smem_u32(&bars->tmem_full[a]), 1);
@@ -200,8 +208,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
+    if (MC) ptx::cluster_sync(); // the peer's barriers are initialised before any multicast
     const uint32_t tmem = bars->tmem_base;
     const int kblocks = p.taps * p.nck;
+    const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
+    // with MC, both CTAs of a cluster walk the same number of tile pairs
+    const int t_end = MC ? ((p.num_tiles + 1) & ~1) : p.num_tiles;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -210,9 +222,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t pa = 0, pb = 0;
             long long issued_a = 0, issued_b = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+            for (int t = blockIdx.x; t < t_end && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t, ph, n, y0, x0);
+                tile_coords(p, t < p.num_tiles ? t : p.num_tiles - 1, ph, n, y0, x0);
                 for (int ky = 0; ky < 3 && !stop; ++ky)
                     for (int c = 0; c < p.nck && !stop; ++c) {
                         if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
@@ -226,12 +238,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             const int slot = STAGES + sb;
                             if (!wait_bar(ptx::smem_u32(&bars->empty[slot]), pb ^ 1, abort, p.err, 1)) { stop = true; break; }
                             uint32_t fbb = ptx::smem_u32(&bars->full[slot]);
-                            ptx::mbar_arrive_expect_tx(fbb, B_BYTES);
-                            ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
+                            ptx::mbar_arrive_expect_tx(fbb, B_BYTES); // both halves land here
+                            if (MC)
+                                ptx::tma_load_3d_mc(ptx::smem_u32(sB + sb * B_STRIDE) + rank * (B_BYTES / 2), &tmB, fbb,
+                                                    c * CK, (int)rank * (BN / 2), ky * 3 + kx, (uint16_t)3);
+                            else
+                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
                             ++issued_b;
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
                     }
+            }
+            if (MC && !*abort && !stop) {
+                // every B slot's last use released by both CTAs: no commit of either
+                // MMA warp is still on its way to the other CTA's barriers
+                for (int i = 0; i < STAGES_B; ++i) {
+                    if (!wait_bar(ptx::smem_u32(&bars->empty[STAGES + sb]), pb ^ 1, abort, p.err, 5)) break;
+                    if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
+                }
             }
             if (*abort || stop) {
                 // let every copy still in flight land before the CTA exits
@@ -305,10 +329,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
-                const uint32_t d = tmem + acc * BN;
+                const uint32_t d = tmem + acc * (MT * BN);
                 bool ok = true;
                 uint32_t accumulate = 0;
                 for (int ky = 0; ky < 3 && ok; ++ky)
@@ -326,13 +350,17 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                             for (int k = 0; k < ROW_BYTES / 32; ++k) {
                                 uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
-                                uint64_t ad = ptx::smem_desc(a0 + kx * ROW_BYTES + k * 32, ROW_BYTES);
-                                if (F8) ptx::mma_f8(d, ad, bd, IDESC, accumulate | (uint32_t)k);
-                                else ptx::mma_bf16(d, ad, bd, IDESC, accumulate | (uint32_t)k);
+#pragma unroll
+                                for (int m = 0; m < MT; ++m) {
+                                    uint64_t ad = ptx::smem_desc(a0 + (m * 130 + kx) * ROW_BYTES + k * 32, ROW_BYTES);
+                                    if (F8) ptx::mma_f8(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
+                                    else ptx::mma_bf16(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
+                                }
                             }
                             accumulate = 1;
                             issued_any = true;
-                            ptx::mma_commit(ptx::smem_u32(&bars->empty[STAGES + sb]));
+                            if (MC) ptx::mma_commit_mc(ptx::smem_u32(&bars->empty[STAGES + sb]), (uint16_t)3);
+                            else ptx::mma_commit(ptx::smem_u32(&bars->empty[STAGES + sb]));
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
                         if (!ok) break;
@@ -398,11 +426,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * 2 * STG_BYTES);
         const int tw = 1 << p.tw_log;
         const int dy = row >> p.tw_log, dx = row & (tw - 1);
-        for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+        for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
-            tile_coords(p, t, ph, n, y0, x0);
+            const bool phantom = t >= p.num_tiles; // pair filler: computed, never stored
+            tile_coords(p, phantom ? p.num_tiles - 1 : t, ph, n, y0, x0);
             int gy = y0 + dy, gx = x0 + dx;
-            bool valid = gy < p.gh && gx < p.gw;
+            bool valid = gy < p.gh && gx < p.gw && !phantom;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
             if (MT == 1 && BN == 32 && p.epi.mode == EPI_RESID) {
                 // Eq. 2 update of a 4-phase transposed conv with 5 outputs (the VIB
@@ -508,7 +537,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int m = 0; m < MT; ++m) {
                 const int rb = m * 128 + q * 32, rm = rb + lane;
                 const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
-                const bool valid = gy < p.gh && gx < p.gw;
+                const bool valid = gy < p.gh && gx < p.gw && !phantom;
                 const int by = y0 + (rb >> p.tw_log), bx = x0 + (rb & (tw - 1));
                 const uint32_t tb = tbase + m * BN;
 #pragma unroll 1
@@ -555,7 +584,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     ptx::fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) {
+                    if (lane == 0 && !phantom) {
                         if (p.mode == MODE_T)
                             ptx::tma_store_5d(&tmC, sbuf, (ph & 1) * p.out_cs + p.out_coff + k0, bx, ph >> 1, by, n);
                         else
@@ -571,7 +600,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // row block m of the tile: accumulator m, pixel rows m * 128 + lane row
             const int rm = m * 128 + row;
             const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
-            const bool valid = gy < p.gh && gx < p.gw;
+            const bool valid = gy < p.gh && gx < p.gw && !phantom;
             const uint32_t tb = tbase + m * BN;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 16) {
@@ -645,6 +674,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     ptx::tc_fence_before();
     __syncthreads();
+    if (MC) ptx::cluster_sync(); // neither CTA leaves while the other may still signal it
     if (warp == 1) {
         __syncwarp();
         ptx::tc_fence_after();
@@ -763,13 +793,16 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &
 // Halo configurations (128-byte operand rows, one accumulator block): A boxes of
 // 130 rows and B slices in separate rings, sized per N tile by hand so that the
 // resident CTAs fill the shared-memory budget.
-template <int BN, int TS> struct HaloCfg {
-    static constexpr uint32_t A = (130 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
+// MT = 2 (N = 256): tiles of 2 x 128 pixels, each weight slice feeds two MMAs; the
+// two accumulators fill TMEM, so the epilogue is not overlapped with the next tile.
+template <int BN, int TS, int MT = 1> struct HaloCfg {
+    static constexpr uint32_t A = (130 * MT * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
     static constexpr uint32_t STG = stg_bytes(BN, TS);
-    static constexpr uint32_t TMEM_COLS = AccCfg<BN, 1>::TMEM_COLS;
+    static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 || TS ? 2 : 3);
-    static constexpr int STAGES = TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
-                                     : (BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
+    static constexpr int STAGES = MT == 2 ? 2
+                                  : TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
+                                       : (BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
     static constexpr int STAGES_B = TS ? (BN >= 256 ? 3 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
                                        : (BN >= 256 ? 4 : (BN >= 128 ? 3 : 4));
     static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
@@ -777,12 +810,12 @@ template <int BN, int TS> struct HaloCfg {
                   "halo config");
 };
 
-template <int BN, int F8, int TS>
+template <int BN, int F8, int TS, int MC, int MT = 1>
 int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                 cudaStream_t st) {
-    using C = HaloCfg<BN, TS>;
+    using C = HaloCfg<BN, TS, MT>;
     constexpr int CK = F8 ? 128 : 64;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, C::STAGES_B, TS>;
+    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8, 1, C::STAGES_B, TS, MC>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -794,6 +827,26 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap 
         FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
     int slots = g_num_sms * C::CTAS;
+    if (MC) {
+        // clusters of two CTAs, tiles in pairs: an even grid over the even tile count
+        slots &= ~1;
+        const int pairs_x2 = (p.num_tiles + 1) & ~1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(pairs_x2 < slots ? pairs_x2 : slots);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        FVV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, mc, p));
+        count_launch();
+        return FVV_OK;
+    }
     int grid = p.num_tiles < slots ? p.num_tiles : slots;
     kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
     count_launch();
@@ -801,23 +854,30 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap 
     return FVV_OK;
 }
 
+// Row blocks per halo tile of the N = 256 layers.  2 halves the weight traffic per
+// FLOP but leaves no TMEM for a second accumulator; measured on the 1080p VIBlock
+// convs it is ~20% slower than 1 (the epilogue no longer overlaps the next tile).
+constexpr int kHaloMT256 = 1;
+
 bool halo_ok(int bn, bool f8) { return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256); }
 
+// N = 256 runs as cluster pairs sharing the weight slices (mb_half: box of 128 rows)
 template <int TS>
-int dispatch_halo_ts(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
-                     const TcParams &p, cudaStream_t st) {
-    if (f8) return launch_halo<256, 1, TS>(ma, mb, mc, p, st);
+int dispatch_halo_ts(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+                     const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
+    if (f8) return launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
     switch (bn) {
-    case 32: return launch_halo<32, 0, TS>(ma, mb, mc, p, st);
-    case 64: return launch_halo<64, 0, TS>(ma, mb, mc, p, st);
-    case 128: return launch_halo<128, 0, TS>(ma, mb, mc, p, st);
-    default: return launch_halo<256, 0, TS>(ma, mb, mc, p, st);
+    case 32: return launch_halo<32, 0, TS, 0>(ma, mb, mc, p, st);
+    case 64: return launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
+    case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
+    default: return launch_halo<256, 0, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
     }
 }
 
-int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
-                  const TcParams &p, cudaStream_t st) {
-    return p.tma_store ? dispatch_halo_ts<1>(bn, f8, ma, mb, mc, p, st) : dispatch_halo_ts<0>(bn, f8, ma, mb, mc, p, st);
+int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+                  const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
+    return p.tma_store ? dispatch_halo_ts<1>(bn, f8, ma, mb, mb_half, mc, p, st)
+                       : dispatch_halo_ts<0>(bn, f8, ma, mb, mb_half, mc, p, st);
 }
 
 template <int TS>
@@ -910,6 +970,10 @@ int tc_prepare(fvv_interp *h, const float *blob) {
         cuuint32_t box[3] = {(cuuint32_t)ck, (cuuint32_t)cop, 1};
         static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
         FVV_TRY(encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, ck * 2));
+        if (cop == 256) {
+            box[1] = (cuuint32_t)(cop / 2);
+            FVV_TRY(encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, ck * 2));
+        }
     }
     if (h->o.precision == FVV_FP8) FVV_TRY(tc_prepare_fp8(h, blob));
     return FVV_OK;
@@ -948,6 +1012,8 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         cuuint32_t box[3] = {128, (cuuint32_t)L.co, 1};
         g_encode_u8 = true;
         int rc = encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, 128);
+        box[1] = (cuuint32_t)(L.co / 2);
+        if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, 128);
         g_encode_u8 = false;
         FVV_TRY(rc);
     }
@@ -989,7 +1055,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     // 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
     const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && ck * es == 128 && halo_ok(bn, f8) &&
                       p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT);
-    if (halo) s = Shape{0, 7};
+    const int halo_mt = bn == 256 ? kHaloMT256 : 1;
+    if (halo) s = Shape{halo_mt - 1, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
@@ -1033,7 +1100,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1};
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1}; // halo: th_ = MT
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
     g_encode_u8 = false;
@@ -1068,7 +1135,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             FVV_TRY(rc);
         }
     }
-    if (halo) return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
+    if (halo)
+        return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half, mc, p, st);
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
 }
 

@@ -35,6 +35,7 @@ struct TcWeights {
     void *w = nullptr;      // device, [phase*taps][Co_pad][Ci_pad] bf16 (or fp8) K-major
     float *scale = nullptr; // FP8: per-output-channel dequantisation scale
     alignas(64) unsigned char map[128] = {}; // host CUtensorMap of w (B operand)
+    alignas(64) unsigned char map_half[128] = {}; // same, box of C_out / 2 rows (cluster-pair loads)
     int ci_pad = 0, co_pad = 0;
 };
 
