@@ -145,7 +145,7 @@ template <int BN, int MT> struct AccCfg {
 
 // F8 = 1: E4M3 operands (kind::f8f6f4, K = 32 per MMA), else BF16 (kind::f16, K = 16);
 // either way one MMA consumes 32 bytes of every operand row.
-// HALO = 1 (stride-1 3x3 taps, MT x 128-pixel tiles, 128-byte rows): one TMA box of
+// HALO = 1 (stride-1 3x3 taps, MT x 128-pixel tiles, 32/64/128-byte rows): one TMA box of
 // MT image rows x 130 pixels per (row tap ky, channel block) serves the three column
 // taps kx, whose A operands start 0, 1, 2 rows into each 130-row block; A boxes
 // (STAGES ring) and B slices (STAGES_B ring) are pipelined separately.  K order is
@@ -165,8 +165,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int ROW_BYTES = CK * ES;
     constexpr uint32_t A_BYTES = HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
-    static_assert(!HALO || (ROW_BYTES == 128 && STAGES + STAGES_B <= 16), "halo config");
-    static_assert(!MC || HALO, "weight multicast runs on the halo path");
+    static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
+    static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -345,8 +345,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             ptx::tc_fence_after();
                             const uint32_t b0 = ptx::smem_u32(sB + sb * B_STRIDE);
                             // column tap kx: the 128 output pixels read box rows kx .. kx + 127.
-                            // The 128B swizzle follows address bits, so a start 1-2 rows
-                            // into the atom needs no base-offset field.
+                            // The swizzle follows address bits, so a start 1-2 rows into
+                            // the swizzle atom needs no base-offset field.
 #pragma unroll
                             for (int k = 0; k < ROW_BYTES / 32; ++k) {
                                 uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
@@ -810,6 +810,41 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
                   "halo config");
 };
 
+// Halo tiles of the narrow layers (C_in = 16 or 32: 32- or 64-byte rows): small
+// boxes, so deep A rings; three CTAs per SM.
+template <int BN, int CK, int TS> struct HaloNarrowCfg {
+    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
+    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr int CTAS = 3, STAGES_B = 4;
+    static constexpr int fit = (int)((kSmemBudget / CTAS - 2048 - STG - STAGES_B * B) / A);
+    static constexpr int STAGES = fit > 12 ? 12 : fit;
+    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
+    static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "narrow halo config");
+};
+
+template <int BN, int CK, int TS>
+int launch_halo_narrow(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+                       cudaStream_t st) {
+    using C = HaloNarrowCfg<BN, CK, TS>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 1, C::STAGES_B, TS, 0>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
 template <int BN, int F8, int TS, int MC, int MT = 1>
 int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                 cudaStream_t st) {
@@ -859,13 +894,18 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap 
 // convs it is ~20% slower than 1 (the epilogue no longer overlaps the next tile).
 constexpr int kHaloMT256 = 1;
 
-bool halo_ok(int bn, bool f8) { return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256); }
+bool halo_ok(int bn, int ck, int es, bool f8) {
+    if (ck * es == 128) return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256);
+    return !f8 && ((bn == 16 && ck == 16) || (bn == 32 && ck == 32));
+}
 
 // N = 256 runs as cluster pairs sharing the weight slices (mb_half: box of 128 rows)
 template <int TS>
-int dispatch_halo_ts(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
                      const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
     if (f8) return launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
+    if (ck == 16) return launch_halo_narrow<16, 16, TS>(ma, mb, mc, p, st);
+    if (ck == 32) return launch_halo_narrow<32, 32, TS>(ma, mb, mc, p, st);
     switch (bn) {
     case 32: return launch_halo<32, 0, TS, 0>(ma, mb, mc, p, st);
     case 64: return launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
@@ -874,10 +914,10 @@ int dispatch_halo_ts(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &
     }
 }
 
-int dispatch_halo(int bn, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
                   const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
-    return p.tma_store ? dispatch_halo_ts<1>(bn, f8, ma, mb, mb_half, mc, p, st)
-                       : dispatch_halo_ts<0>(bn, f8, ma, mb, mb_half, mc, p, st);
+    return p.tma_store ? dispatch_halo_ts<1>(bn, ck, f8, ma, mb, mb_half, mc, p, st)
+                       : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mc, p, st);
 }
 
 template <int TS>
@@ -1053,7 +1093,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     }
     // default tile of the 3x3 stride-1 layers with 128-byte operand rows: one row of
     // 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
-    const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && ck * es == 128 && halo_ok(bn, f8) &&
+    const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
                       p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT);
     const int halo_mt = bn == 256 ? kHaloMT256 : 1;
     if (halo) s = Shape{halo_mt - 1, 7};
@@ -1136,7 +1176,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         }
     }
     if (halo)
-        return dispatch_halo(bn, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half, mc, p, st);
+        return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half, mc, p, st);
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
 }
 

@@ -5,7 +5,7 @@ rows run, on grids at least 96 pixels wide, on tiles of one 128-pixel row whose
 A operand is ONE box of 130 pixels per (row tap, channel block): the three
 column taps read it 0, 1, 2 rows in.  Checks:
 
-* each such layer alone on wide ragged grids (last tile partly outside the
+* each such layer (128-, 64- and 32-byte operand rows) alone on wide ragged grids (last tile partly outside the
   grid, zero padding on both sides) against the oracle's conv of the same
   bf16-rounded input and weights, the bar of the per-layer tests;
 * the 256-channel layers run as clusters of two CTAs sharing each weight slice
@@ -26,7 +26,9 @@ from tests.gpu_common import blob, pair
 
 pytestmark = pytest.mark.gpu
 
-HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3"]
+# 128-byte rows (C_in >= 64) and the narrow 32- / 64-byte rows (C_in = 16, 32)
+HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3", "ctx.c1", "ctx.c3",
+               "ref.e0b"]
 
 
 @pytest.fixture(scope="module")
