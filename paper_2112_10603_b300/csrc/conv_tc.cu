@@ -800,11 +800,13 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
     static constexpr uint32_t STG = stg_bytes(BN, TS);
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 || TS ? 2 : 3);
+    // N = 256: one A box feeds 3 weight slices (~0.8 us of MMA), so two A stages
+    // suffice and the weight ring gets the rest (its slices are 32 KB).
     static constexpr int STAGES = MT == 2 ? 2
-                                  : TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
-                                       : (BN >= 256 ? 4 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
-    static constexpr int STAGES_B = TS ? (BN >= 256 ? 3 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
-                                       : (BN >= 256 ? 4 : (BN >= 128 ? 3 : 4));
+                                  : TS ? (BN >= 256 ? 2 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
+                                       : (BN >= 256 ? 2 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
+    static constexpr int STAGES_B = TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
+                                       : (BN >= 256 ? 5 : (BN >= 128 ? 3 : 4));
     static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
     static_assert(CTAS * SMEM <= kSmemBudget + 8 * 1024 && CTAS * TMEM_COLS <= 512 && STAGES >= 2 && STAGES_B >= 2,
                   "halo config");
