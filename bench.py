@@ -33,6 +33,10 @@ TS = [k / 8 for k in range(1, 8)]
 METRIC = "1080p virtual views/s"
 SCENE_SEED, WEIGHT_SEED, MAX_DISP = 2, 0, 64.0
 FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+# DRAM bytes (read + write) of one vib2.m launch at this workload, from one ncu capture
+# each (profiles/conv_tc_halo_pair_vib2_m1_1080p_7views.md and
+# profiles/conv_tc_fp8_halo_pair_vib2_m1_1080p_7views.md); refresh when the kernel changes
+TRAFFIC_VIB2_M = {"bf16": 469_191_168 + 430_624_512, "fp8": 234_666_496 + 196_963_072}
 
 
 def peaks():
@@ -428,27 +432,31 @@ def main():
     e2e = {"value": len(TS) * world / e2e_s, "unit": "views/s",
            "h2d_bytes_per_step": 2 * left.nbytes, "d2h_bytes_per_step": len(TS) * left.nbytes}
 
-    # roofline of the dominant kernel (the convolution kernel family)
+    # roofline of the dominant kernel: the VIBlock 3x3 256 -> 256 convolutions of the
+    # full-resolution stage (vib2.m0-m5: six identical launches, the largest share of
+    # the step) on the tensor-core paths; the whole conv family is reported beside it
     pk, pk_kind = peaks()
     conv_ms, conv_fl = float(lms.sum()), float(lfl.sum())
+    names = [m[0] for m in weights.manifest()]
+    vib2m = [names.index(f"vib2.m{k}") for k in range(6)]
+    m_ms, m_fl, m_n = float(lms[vib2m].sum()), float(lfl[vib2m].sum()), int(lln[vib2m].sum())
     if args.precision == "fp32":
-        roof = {"bound": "alu", "kernel": "conv_simt_kernel (FP32 FFMA implicit GEMM)",
+        roof = {"bound": "alu", "kernel": "conv_simt_kernel (FP32 FFMA implicit GEMM), all layers",
                 "achieved": conv_fl / (conv_ms / 1e3) / 1e12, "peak": FP32_FFMA_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+                "unit": "TFLOP/s", "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz", "traffic": None}
     elif args.precision == "fp8":
-        # the 256-channel VIB convs run E4M3; their peak is 2x BF16 (nominal 4.5 vs 2.25 PF)
-        f8 = [i for i, m in enumerate(weights.manifest()) if i < 30 and 2 <= i % 10 <= 7]
-        f8_ms, f8_fl = float(lms[f8].sum()), float(lfl[f8].sum())
-        roof = {"bound": "tensor", "kernel": "conv_tc_kernel FP8 (tcgen05 kind::f8f6f4), the 18 VIB m-convs",
-                "achieved": f8_fl / (f8_ms / 1e3) / 1e12, "peak": 2 * pk["bf16_tflops_sustained"],
+        roof = {"bound": "tensor", "kernel": "conv_tc_kernel E4M3 halo, cluster pairs (tcgen05 kind::f8f6f4): vib2.m0-m5",
+                "achieved": m_fl / (m_ms / 1e3) / 1e12, "peak": 2 * pk["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained x 2 (fp8/bf16 nominal ratio)",
+                "traffic": TRAFFIC_VIB2_M.get("fp8"), "launch_us": m_ms / max(m_n, 1) * 1e3,
                 "all_convs_tflops": conv_fl / (conv_ms / 1e3) / 1e12}
     else:
-        roof = {"bound": "tensor", "kernel": "conv_tc_kernel (tcgen05 BF16 implicit GEMM)",
-                "achieved": conv_fl / (conv_ms / 1e3) / 1e12, "peak": pk["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained"}
+        roof = {"bound": "tensor", "kernel": "conv_tc_kernel BF16 halo, cluster pairs (tcgen05 kind::f16): vib2.m0-m5",
+                "achieved": m_fl / (m_ms / 1e3) / 1e12, "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained",
+                "traffic": TRAFFIC_VIB2_M.get("bf16"), "launch_us": m_ms / max(m_n, 1) * 1e3,
+                "all_convs_tflops": conv_fl / (conv_ms / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
     roof["conv_share_of_step"] = conv_ms / ms_total
     roof["launches"] = int(lln.sum())
 
