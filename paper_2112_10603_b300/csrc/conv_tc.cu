@@ -156,8 +156,10 @@ template <int BN, int MT> struct AccCfg {
 // rings, halving the weight traffic from L2.  A slot of the B ring is released by
 // both CTAs' MMA commits; tiles go in pairs (a pair's odd last member is computed
 // on a clamped tile and not stored).
+// GRP = 1 (halo, small N): one stage holds a (row tap, channel block)'s A box AND its
+// three weight slices, so the MMA thread syncs once per 3 x (row bytes / 32) MMAs.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0>
+          int MC = 0, int GRP = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
@@ -167,6 +169,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
     static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
+    static_assert(!GRP || (HALO && !MC), "grouped stages run on the halo path");
+    constexpr uint32_t G_STRIDE = A_STRIDE + 3 * B_STRIDE; // grouped stage: A box + 3 weight slices
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -174,10 +178,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * A_STRIDE;
+    uint8_t *sB = smem + STAGES * (GRP ? G_STRIDE : A_STRIDE);
     // epilogue staging: per epilogue warp two buffers of 32 rows x STG_ROW bytes
     constexpr uint32_t STG_ROW = BN * 2 < 128 ? BN * 2 : 128, STG_BYTES = 32 * STG_ROW;
-    uint8_t *stg = sB + (HALO ? STAGES_B : STAGES) * B_STRIDE;
+    uint8_t *stg = sB + (GRP ? 0 : (HALO ? STAGES_B : STAGES)) * B_STRIDE;
     Bars *bars = (Bars *)(stg + (TS ? 8 * STG_BYTES : 0));
     volatile int *abort = &bars->abort;
 
@@ -185,7 +189,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         // halo: full/empty[0, STAGES) = A ring, [STAGES, STAGES + STAGES_B) = B ring
-        for (int s = 0; s < (HALO ? STAGES + STAGES_B : STAGES); ++s) {
+        for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), MC && s >= STAGES ? 2 : 1);
         }
@@ -217,7 +221,38 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0 && HALO) {
+        if (lane == 0 && GRP) {
+            int s = 0;
+            uint32_t ph_bit = 0;
+            long long issued = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+                int ph, n, y0, x0;
+                tile_coords(p, t, ph, n, y0, x0);
+                for (int ky = 0; ky < 3 && !stop; ++ky)
+                    for (int c = 0; c < p.nck; ++c) {
+                        if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
+                        const uint32_t fs = ptx::smem_u32(&bars->full[s]);
+                        ptx::mbar_arrive_expect_tx(fs, A_BYTES + 3 * B_BYTES);
+                        const uint32_t base = ptx::smem_u32(sA + s * G_STRIDE);
+                        ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx)
+                            ptx::tma_load_3d(base + A_STRIDE + kx * B_STRIDE, &tmB, fs, c * CK, 0, ky * 3 + kx);
+                        ++issued;
+                        if (++s == STAGES) { s = 0; ph_bit ^= 1; }
+                    }
+            }
+            if (*abort || stop) {
+                // let every copy still in flight land before the CTA exits
+                for (int i = 0; i < STAGES && i < issued; ++i) {
+                    long long k = issued - 1 - i;
+                    long long t0 = clock64();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full[k % STAGES]), (uint32_t)((k / STAGES) & 1)) &&
+                           clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        } else if (lane == 0 && HALO) {
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             long long issued_a = 0, issued_b = 0;
@@ -323,7 +358,51 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0 && HALO) {
+        if (lane == 0 && GRP) {
+            int s = 0;
+            uint32_t ph_bit = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem + acc * (MT * BN);
+                bool ok = true;
+                uint32_t accumulate = 0;
+                for (int g = 0; g < 3 * p.nck; ++g) { // (ky, channel block) in K order
+                    if (!wait_bar(ptx::smem_u32(&bars->full[s]), ph_bit, abort, p.err, 3)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t a0 = ptx::smem_u32(sA + s * G_STRIDE);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const uint32_t b0 = a0 + A_STRIDE + kx * B_STRIDE;
+#pragma unroll
+                        for (int k = 0; k < ROW_BYTES / 32; ++k) {
+                            uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
+#pragma unroll
+                            for (int m = 0; m < MT; ++m) {
+                                uint64_t ad = ptx::smem_desc(a0 + (m * 130 + kx) * ROW_BYTES + k * 32, ROW_BYTES);
+                                if (F8) ptx::mma_f8(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
+                                else ptx::mma_bf16(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
+                            }
+                        }
+                        accumulate = 1;
+                    }
+                    issued_any = true;
+                    ptx::mma_commit(ptx::smem_u32(&bars->empty[s]));
+                    if (++s == STAGES) { s = 0; ph_bit ^= 1; }
+                }
+                if (!ok) break;
+                ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
+                if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
+            }
+            if (*abort && issued_any) {
+                ptx::mma_commit(ptx::smem_u32(&bars->drain));
+                long long t0 = clock64();
+                while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->drain), 0) && clock64() - t0 < kWaitCycles) {}
+            }
+        } else if (lane == 0 && HALO) {
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             int acc = 0;
@@ -847,6 +926,42 @@ int launch_halo_narrow(const CUtensorMap &ma, const CUtensorMap &mb, const CUten
     return FVV_OK;
 }
 
+// Grouped halo stages (a stage = one A box + its three weight slices), used where
+// measured faster: the all-phase transposed conv with N = 64 (RefineNet d3).
+template <int BN, int CK, int TS> struct HaloGrpCfg {
+    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u, G = A + 3 * B;
+    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / G); }
+    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 2 ? ctas_for(c - 1) : c; }
+    static constexpr int CTAS = ctas_for(BN <= 32 ? 3 : 2);
+    static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
+    static constexpr size_t SMEM = (size_t)STAGES * G + STG + sizeof(Bars) + 1024;
+    static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "grouped halo config");
+};
+
+template <int BN, int CK, int TS>
+int launch_halo_grp(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+                    cudaStream_t st) {
+    using C = HaloGrpCfg<BN, CK, TS>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 1, 2, TS, 0, 1>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
 template <int BN, int F8, int TS, int MC, int MT = 1>
 int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                 cudaStream_t st) {
@@ -910,7 +1025,8 @@ int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUten
     if (ck == 32) return launch_halo_narrow<32, 32, TS>(ma, mb, mc, p, st);
     switch (bn) {
     case 32: return launch_halo<32, 0, TS, 0>(ma, mb, mc, p, st);
-    case 64: return launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
+    case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb, mc, p, st)
+                                             : launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
     case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
     default: return launch_halo<256, 0, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
     }
