@@ -891,43 +891,10 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
                   "halo config");
 };
 
-// Halo tiles of the narrow layers (C_in = 16 or 32: 32- or 64-byte rows): small
-// boxes, so deep A rings; three CTAs per SM.
-template <int BN, int CK, int TS> struct HaloNarrowCfg {
-    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u;
-    static constexpr uint32_t STG = stg_bytes(BN, TS);
-    static constexpr int CTAS = 3, STAGES_B = 4;
-    static constexpr int fit = (int)((kSmemBudget / CTAS - 2048 - STG - STAGES_B * B) / A);
-    static constexpr int STAGES = fit > 12 ? 12 : fit;
-    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
-    static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "narrow halo config");
-};
-
-template <int BN, int CK, int TS>
-int launch_halo_narrow(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
-                       cudaStream_t st) {
-    using C = HaloNarrowCfg<BN, CK, TS>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 1, C::STAGES_B, TS, 0>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-        attr_set = true;
-    }
-    if (!g_num_sms) {
-        int dev;
-        FVV_CHECK_CUDA(cudaGetDevice(&dev));
-        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    int slots = g_num_sms * C::CTAS;
-    int grid = p.num_tiles < slots ? p.num_tiles : slots;
-    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
-    count_launch();
-    FVV_CHECK_CUDA(cudaGetLastError());
-    return FVV_OK;
-}
-
-// Grouped halo stages (a stage = one A box + its three weight slices), used where
-// measured faster: the all-phase transposed conv with N = 64 (RefineNet d3).
+// Grouped halo stages (a stage = one A box + its three weight slices) for the small-N
+// layers: the narrow 16/32-channel convs, the VIB t1 and RefineNet d3 transposed convs
+// (measured 3-18% faster than split A/B rings; the 64-column convs with the
+// TMA-store epilogue keep split rings, which fit two CTAs per SM).
 template <int BN, int CK, int TS> struct HaloGrpCfg {
     static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u, G = A + 3 * B;
     static constexpr uint32_t STG = stg_bytes(BN, TS);
@@ -1021,10 +988,10 @@ template <int TS>
 int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
                      const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
     if (f8) return launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
-    if (ck == 16) return launch_halo_narrow<16, 16, TS>(ma, mb, mc, p, st);
-    if (ck == 32) return launch_halo_narrow<32, 32, TS>(ma, mb, mc, p, st);
+    if (ck == 16) return launch_halo_grp<16, 16, TS>(ma, mb, mc, p, st);
+    if (ck == 32) return launch_halo_grp<32, 32, TS>(ma, mb, mc, p, st);
     switch (bn) {
-    case 32: return launch_halo<32, 0, TS, 0>(ma, mb, mc, p, st);
+    case 32: return launch_halo_grp<32, 64, TS>(ma, mb, mc, p, st);
     case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb, mc, p, st)
                                              : launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
     case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
