@@ -215,8 +215,11 @@ def serve_once(s, fvv, n_users, rate_hz, seconds, seed):
 
     def reap(u, wait=False):
         keep = []
+        deadline = time.perf_counter() + 60.0     # a ticket that never finishes fails the run
         for tk in outstanding.get(u, []):
             while True:
+                if wait and time.perf_counter() > deadline:
+                    raise RuntimeError("server: a request did not finish within 60 s")
                 try:
                     st, _, l = fvv.fvv_serve_poll(s, tk)
                 except fvv.FvvError:          # superseded
@@ -294,6 +297,116 @@ def run_serve(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve_dense(args, rank, world, local):
+    """Dense serving (the paper's per-instant view set): 9-camera rig at 1080p, new
+    frames every 1/30 s (two frame sets alternating), 2^4 - 1 = 15 views per pair
+    rendered once per instant; users' requests snap t to k/16 and are answered from
+    the newest complete set.  Run at 4 and at 64 users: the GPU work per instant
+    (instants/s, views rendered/s) should not depend on the user count."""
+    import threading
+    import torch
+    import paper_2112_10603_b300 as fvv
+    from paper_2112_10603_b300 import build as fvv_build
+    from synth import scene, weights
+    fvv_build.build()
+    torch.cuda.set_device(local)
+    n_cams, (h, w) = 9, (1080, 1920)
+    frames = [[torch.from_numpy(c).cuda() for c in scene.rig(5 + i, h, w, n_cams=n_cams, max_disp=MAX_DISP)]
+              for i in range(2)]
+    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=1, res_h=[h], res_w=[w], n_cams=n_cams,
+                                    slots_per_res=2, max_batch=15, dense_levels=4)
+    s = fvv.fvv_serve_create(weights.he_init(WEIGHT_SEED), cfg)
+    runs = []
+    try:
+        fvv.fvv_serve_set_frames(s, 0, 0, frames[0])
+        for users, secs in ((4, 3.0), (64, args.serve_seconds), (4, 3.0)):
+            stop = threading.Event()
+            inst = [1]
+
+            def feeder():
+                while not stop.is_set():
+                    time.sleep(1 / 30)
+                    fvv.fvv_serve_set_frames(s, inst[0], 0, frames[inst[0] % 2])
+                    inst[0] += 1
+
+            th = threading.Thread(target=feeder)
+            base = fvv.fvv_serve_stats_get(s)
+            th.start()
+            t0 = time.perf_counter()
+            r = serve_once_dense(s, fvv, users, 30.0, secs, 7 + users, n_cams - 1)
+            stop.set()
+            th.join()
+            wall = time.perf_counter() - t0
+            st = fvv.fvv_serve_stats_get(s)
+            r["instants_per_s"] = (st["dense_instants"] - base["dense_instants"]) / wall
+            r["views_rendered_per_s"] = r["instants_per_s"] * (n_cams - 1) * 15
+            r["frames_offered_per_s"] = (inst[0] - 1) / wall
+            runs.append(r)
+    finally:
+        fvv.fvv_serve_destroy(s)
+    main = runs[1]
+    line = {"metric": "dense serving: virtual views rendered/s (9-camera rig, 1080p, 15 views per pair per instant)",
+            "value": main["views_rendered_per_s"], "unit": "views/s", "n_gpus": world, "higher_is_better": True,
+            "dtype": "bf16", "data": "synthetic 9-camera rig (two alternating frame sets), Poisson viewpoint requests",
+            "config": {"workload": "serve-dense: frames at 30 Hz, 8 pairs x 15 views per instant, 64 users x 30 Hz "
+                                   "requests snapped to t = k/16", "seconds": args.serve_seconds,
+                       "slots": 2, "max_batch": 15},
+            "instants_per_s": main["instants_per_s"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "answered_req_per_s": main["completed_req_per_s"],
+            "user_count_invariance": [{k: r[k] for k in ("users", "instants_per_s", "views_rendered_per_s",
+                                                         "completed_req_per_s", "p50_ms", "p99_ms")} for r in runs]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serve_once_dense(s, fvv, n_users, rate_hz, seconds, seed, n_pairs):
+    """Open-loop requests for the dense server; every ticket is polled to completion."""
+    rng = np.random.default_rng(seed)
+    events = []
+    for u in range(n_users):
+        t = rng.exponential(1 / rate_hz)
+        while t < seconds:
+            events.append((t, u))
+            t += rng.exponential(1 / rate_hz)
+    events.sort()
+    pending, lat = [], []
+
+    def reap(wait):
+        keep = []
+        deadline = time.perf_counter() + 60.0     # a ticket that never finishes fails the run
+        for tk in pending:
+            while True:
+                try:
+                    st, _, l = fvv.fvv_serve_poll(s, tk)
+                except fvv.FvvError:          # superseded
+                    fvv.fvv_serve_release(s, tk)
+                    break
+                if st == 0:
+                    lat.append(l)
+                    fvv.fvv_serve_release(s, tk)
+                    break
+                if not wait:
+                    keep.append(tk)
+                    break
+                if time.perf_counter() > deadline:
+                    raise RuntimeError("dense server: a request did not finish within 60 s")
+                time.sleep(0.0005)
+        pending[:] = keep
+
+    t0 = time.perf_counter()
+    for when, u in events:
+        while time.perf_counter() - t0 < when:
+            time.sleep(0.0002)
+        pending.append(fvv.fvv_serve_submit(s, u, int(rng.integers(0, n_pairs)), float(rng.uniform(0, 1)), 0))
+        if len(pending) > 256:
+            reap(False)
+    reap(True)
+    wall = time.perf_counter() - t0
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"users": n_users, "completed_req_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99))}
+
+
 def rank_pair_seed(rank: int) -> int:
     """Each rank synthesises its own camera pair (weak scaling: the work per GPU is fixed)."""
     return SCENE_SEED + rank
@@ -332,7 +445,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--views", type=int, default=7, help="views per step (t = k/(views+1))")
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed steps (for profiling)")
-    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve"],
+    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve", "serve-dense"],
                     help="pair: the headline 1-pair 7-view step; rig: batched 9-camera instants; "
                          "serve: 64-user mixed-resolution serving")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -349,6 +462,8 @@ def main():
         return run_rig(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
+    if args.workload == "serve-dense":
+        return run_serve_dense(args, rank, world, local)
 
     import torch
     import paper_2112_10603_b300 as fvv

@@ -214,7 +214,19 @@ void fvv_interp_destroy(fvv_interp *h);
  * `pool_views` buffers, cut to fit `hbm_budget` (bytes, 0 = no limit) after the
  * slots' workspaces; an empty pool makes submit return FVV_EBUSY.  The server is
  * thread-safe.  With fake_ms_per_view > 0 no GPU is used (batches just take
- * fake_ms_per_view per view on the host): for testing the scheduling logic. */
+ * fake_ms_per_view per view on the host): for testing the scheduling logic.
+ *
+ * Dense mode (dense_levels = n > 0; the paper's serving scheme, Sec. 3.2 and the
+ * n-stage dense views of Sec. 4.2): for every capture instant the server renders
+ * the fixed set t = k / 2^n, k = 1 .. 2^n - 1, of every camera pair once (batches
+ * of whole pairs, 2^n - 1 <= max_batch), into one of two per-resolution stores
+ * (the newest complete instant is served from one while the next renders into the
+ * other).  A request's t snaps to the nearest k / 2^n; k = 0 or 2^n answer with the
+ * camera frame itself.  A request is answered at once from the newest complete set
+ * when that set belongs to the newest frames (set_frames), else by the first set
+ * completed after it arrives; the GPU load does not depend on the number of users.  Its view pointer stays valid until the server starts rendering the
+ * second instant after it; release() only forgets the ticket.  Frames passed to
+ * set_frames must stay valid until their instant has been rendered. */
 
 #define FVV_SERVE_MAX_RES 4
 
@@ -228,12 +240,14 @@ typedef struct {
     int pool_views;                 /* output buffers per resolution (before the budget cut) */
     size_t hbm_budget;              /* device bytes the server may hold; 0 = unlimited */
     double fake_ms_per_view;        /* > 0: no GPU, simulated batches (tests) */
+    int dense_levels;               /* 0: render each request; n > 0: dense mode, 2^n - 1 views per pair */
 } fvv_serve_cfg;
 
 typedef struct {
     long long submitted, completed, superseded, rejected, failed, batches, batched_views, queued;
     double p50_ms, p99_ms, max_ms;  /* latency submit -> view ready, completed requests */
     size_t device_bytes;
+    long long dense_instants;       /* dense mode: instants whose view set was rendered */
 } fvv_serve_stats;
 
 typedef struct fvv_server fvv_server;

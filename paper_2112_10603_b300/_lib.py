@@ -226,14 +226,15 @@ class fvv_serve_cfg(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_res", ctypes.c_int),
                 ("res_h", ctypes.c_int * FVV_SERVE_MAX_RES), ("res_w", ctypes.c_int * FVV_SERVE_MAX_RES),
                 ("n_cams", ctypes.c_int), ("slots_per_res", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("pool_views", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("fake_ms_per_view", ctypes.c_double)]
+                ("pool_views", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("fake_ms_per_view", ctypes.c_double),
+                ("dense_levels", ctypes.c_int)]
 
 
 class fvv_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in ("submitted", "completed", "superseded", "rejected", "failed",
                                                    "batches", "batched_views", "queued")] + \
                [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("dense_instants", ctypes.c_longlong)]
 
 
 def _serve_sigs(L):

@@ -20,7 +20,11 @@
 //  * a slot remembers which frame instant its pyramid/ContextNet features belong
 //    to and skips recomputing them for the next batch of the same instant;
 //  * completion is signalled by a host callback on the slot stream, which stamps
-//    the latency (submit -> views in their output buffers).
+//    the latency (submit -> views in their output buffers);
+//  * dense mode (dense_levels = n): per instant the fixed set t = k / 2^n of every
+//    pair is rendered once (batches of whole pairs) into one of two stores; requests
+//    snap t to that grid and are answered from the store of the newest frames, so
+//    the GPU work per instant does not depend on the number of users.
 // With cfg.fake_ms_per_view > 0 nothing touches the GPU: a batch "runs" for
 // fake_ms_per_view x views milliseconds on the scheduler thread, so the queueing,
 // supersession, admission and latency logic can be tested on any machine.
@@ -50,6 +54,8 @@ struct Request {
     int user = 0, pair = 0, res = 0, state = RQ_QUEUED, buf = -1;
     float t = 0.f;
     double t_submit = 0, t_done = 0;
+    int k = 0;                   // dense mode: snapped index, t = k / 2^n
+    const float *out = nullptr;  // dense mode: the view (store or camera frame)
 };
 
 struct Batch;
@@ -70,6 +76,15 @@ struct Res {
     std::deque<uint64_t> queue;
     std::vector<const float *> cams;
     long long frames_id = -1;
+    // dense mode: two stores of n_pairs x (2^n - 1) views
+    float *dstore[2] = {nullptr, nullptr};
+    long long d_inst[2] = {-1, -1};  // complete instant held by each store
+    int d_cur = -1;                  // store of the newest complete instant
+    long long d_render = -1;         // instant being rendered (-1: none)
+    int d_buf = 0;                   // store it renders into
+    std::vector<const float *> d_cams;
+    int d_next_pair = 0, d_pairs_done = 0;
+    std::vector<uint64_t> d_waiting; // tickets waiting for the newest frames' views
 };
 
 } // namespace
@@ -88,6 +103,8 @@ struct fvv_server {
     std::unordered_map<int, uint64_t> queued_of_user; // user -> ticket still queued
     uint64_t next_ticket = 1;
     fvv_serve_stats st{};
+    int nd = 0;          // dense mode: views per pair (2^n - 1), 0 = on-demand mode
+    int n_pairs = 0;
     std::vector<double> lat; // completed latencies (ms)
     size_t dev_bytes = 0;
 };
@@ -128,6 +145,100 @@ void finish_batch(Batch *b, bool ok) {
 }
 
 void CUDART_CB batch_done_cb(void *p) { finish_batch(static_cast<Batch *>(p), true); }
+
+// ---- dense mode ------------------------------------------------------------
+const float *dense_ptr(const fvv_server *s, const Res &R, int store, int pair, int k) {
+    const size_t view = (size_t)R.H * R.W * 3;
+    return R.dstore[store] + ((size_t)pair * s->nd + (k - 1)) * view;
+}
+
+// Answer a dense request from the newest complete store (lock held).
+void dense_answer(fvv_server *s, Request &r, double t) {
+    Res &R = s->res[r.res];
+    r.out = dense_ptr(s, R, R.d_cur, r.pair, r.k);
+    r.state = RQ_DONE;
+    r.t_done = t;
+    s->st.completed++;
+    s->lat.push_back(t - r.t_submit);
+}
+
+struct RenderBatch {
+    fvv_server *s;
+    int res, slot, n_pairs;
+    long long instant;
+    bool ok;
+};
+
+void finish_render(RenderBatch *b) {
+    fvv_server *s = b->s;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        Res &R = s->res[b->res];
+        R.slots[b->slot].busy = false;
+        s->st.batches++;
+        s->st.batched_views += (long long)b->n_pairs * s->nd;
+        if (!b->ok) {
+            s->st.failed++;
+            R.d_render = -1; // retried by the scheduler on the newest frames
+        } else if (b->instant == R.d_render && (R.d_pairs_done += b->n_pairs) == s->n_pairs) {
+            R.d_inst[R.d_buf] = R.d_render;
+            R.d_cur = R.d_buf;
+            R.d_render = -1;
+            s->st.dense_instants++;
+            // every waiting request is answered by the first set completed after it
+            // arrived, even when newer frames have been set meanwhile (frames may
+            // arrive faster than a whole set renders: no request starves)
+            double t = now_ms();
+            for (uint64_t tk : R.d_waiting) {
+                auto it = s->reqs.find(tk);
+                if (it != s->reqs.end() && it->second.state == RQ_QUEUED) {
+                    auto q = s->queued_of_user.find(it->second.user);
+                    if (q != s->queued_of_user.end() && q->second == tk) s->queued_of_user.erase(q);
+                    dense_answer(s, it->second, t);
+                }
+            }
+            R.d_waiting.clear();
+        }
+    }
+    s->cv.notify_all();
+    delete b;
+}
+
+void CUDART_CB render_done_cb(void *p) { finish_render(static_cast<RenderBatch *>(p)); }
+
+// Render pairs [p0, p0 + np) of instant `inst` on a free slot (lock not held).
+void launch_render(fvv_server *s, int r, int slot, int p0, int np, long long inst, std::vector<const float *> cams,
+                   float *store) {
+    Res &R = s->res[r];
+    Slot &sl = R.slots[slot];
+    RenderBatch *b = new RenderBatch{s, r, slot, np, inst, true};
+    if (s->cfg.fake_ms_per_view > 0) {
+        std::this_thread::sleep_for(
+            std::chrono::microseconds((long long)(1000.0 * s->cfg.fake_ms_per_view * np * s->nd)));
+        finish_render(b);
+        return;
+    }
+    const int nd = s->nd, levels = s->cfg.dense_levels;
+    std::vector<int> pair_left(np), offs(np + 1);
+    std::vector<float> t((size_t)np * nd);
+    for (int i = 0; i < np; ++i) {
+        pair_left[i] = p0 + i;
+        offs[i] = i * nd;
+        for (int k = 1; k <= nd; ++k) t[(size_t)i * nd + k - 1] = (float)k / (float)(1 << levels);
+    }
+    offs[np] = np * nd;
+    sl.h->skip_cams = sl.frames_id == inst ? 1 : 0;
+    const size_t view = (size_t)R.H * R.W * 3;
+    int rc = fvv_interp_run_batch(sl.h, cams.data(), (int)cams.size(), pair_left.data(), offs.data(), t.data(), np,
+                                  store + (size_t)p0 * nd * view, sl.st);
+    sl.h->skip_cams = 0;
+    sl.frames_id = rc == FVV_OK ? inst : -1;
+    if (rc == FVV_OK && cudaLaunchHostFunc(sl.st, render_done_cb, b) != cudaSuccess) rc = FVV_ECUDA;
+    if (rc != FVV_OK) {
+        b->ok = false;
+        finish_render(b);
+    }
+}
 
 // Launch one batch on a free slot (called without the lock held).
 int launch_batch(fvv_server *s, Batch *b, const std::vector<Request> &rq, const std::vector<const float *> &cams,
@@ -177,6 +288,40 @@ void scheduler(fvv_server *s) {
         bool launched = false;
         for (int r = 0; r < (int)s->res.size() && !s->stop; ++r) {
             Res &R = s->res[r];
+            if (s->nd > 0) {
+                // start rendering the newest frames once the previous render is over
+                if (R.d_render < 0 && R.frames_id >= 0 && !R.cams.empty() &&
+                    (R.d_cur < 0 || R.d_inst[R.d_cur] != R.frames_id)) {
+                    bool idle = true;
+                    for (auto &sl : R.slots) idle = idle && !sl.busy;
+                    if (idle) {
+                        R.d_render = R.frames_id;
+                        R.d_buf = R.d_cur == 0 ? 1 : 0;
+                        R.d_inst[R.d_buf] = -1;
+                        R.d_cams = R.cams;
+                        R.d_next_pair = 0;
+                        R.d_pairs_done = 0;
+                    }
+                }
+                while (R.d_render >= 0 && R.d_next_pair < s->n_pairs && !s->stop) {
+                    int k = -1;
+                    for (int j = 0; j < (int)R.slots.size(); ++j)
+                        if (!R.slots[j].busy) { k = j; break; }
+                    if (k < 0) break;
+                    const int per = std::max(1, s->cfg.max_batch / s->nd);
+                    const int p0 = R.d_next_pair, np = std::min(per, s->n_pairs - p0);
+                    R.d_next_pair += np;
+                    R.slots[k].busy = true;
+                    std::vector<const float *> cams = R.d_cams;
+                    long long inst = R.d_render;
+                    float *store = R.dstore[R.d_buf];
+                    lk.unlock();
+                    launch_render(s, r, k, p0, np, inst, cams, store);
+                    lk.lock();
+                    launched = true;
+                }
+                continue;
+            }
             int free_slot = -1;
             for (int k = 0; k < (int)R.slots.size(); ++k)
                 if (!R.slots[k].busy) { free_slot = k; break; }
@@ -238,8 +383,14 @@ int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg 
         cfg->n_cams < 2 || cfg->pool_views < 1) {
         set_error("bad server configuration"); return FVV_EINVAL;
     }
+    if (cfg->dense_levels < 0 || cfg->dense_levels > 8 ||
+        (cfg->dense_levels > 0 && (1 << cfg->dense_levels) - 1 > cfg->max_batch)) {
+        set_error("dense_levels must give 2^n - 1 <= max_batch views per pair"); return FVV_EINVAL;
+    }
     fvv_server *s = new fvv_server();
     s->cfg = *cfg;
+    s->nd = cfg->dense_levels > 0 ? (1 << cfg->dense_levels) - 1 : 0;
+    s->n_pairs = cfg->n_cams - 1;
     s->res.resize(cfg->n_res);
     int rc = FVV_OK;
     for (int r = 0; r < cfg->n_res && rc == FVV_OK; ++r) {
@@ -266,7 +417,7 @@ int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg 
         }
     }
     // output pool: pool_views per resolution, cut to what the HBM budget leaves
-    for (int r = 0; r < cfg->n_res && rc == FVV_OK && cfg->fake_ms_per_view <= 0; ++r) {
+    for (int r = 0; r < cfg->n_res && rc == FVV_OK && cfg->fake_ms_per_view <= 0 && s->nd == 0; ++r) {
         Res &R = s->res[r];
         size_t view = (size_t)R.H * R.W * 12;
         int n = cfg->pool_views;
@@ -280,6 +431,21 @@ int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg 
         for (auto &p : R.pool)
             if (cudaMalloc(&p, view) != cudaSuccess) { set_error("server: pool allocation failed"); rc = FVV_ENOMEM; break; }
         s->dev_bytes += (size_t)n * view;
+    }
+    // dense stores: two per resolution (fake mode: distinct never-dereferenced bases)
+    for (int r = 0; r < cfg->n_res && rc == FVV_OK && s->nd > 0; ++r) {
+        Res &R = s->res[r];
+        const size_t bytes = (size_t)s->n_pairs * s->nd * R.H * R.W * 12;
+        for (int b = 0; b < 2 && rc == FVV_OK; ++b) {
+            if (cfg->fake_ms_per_view > 0) {
+                R.dstore[b] = reinterpret_cast<float *>((uintptr_t)(r * 2 + b + 1) << 40);
+            } else if (cudaMalloc(&R.dstore[b], bytes) != cudaSuccess) {
+                R.dstore[b] = nullptr;
+                set_error("server: dense store allocation failed"); rc = FVV_ENOMEM;
+            } else {
+                s->dev_bytes += bytes;
+            }
+        }
     }
     if (rc != FVV_OK) { fvv_serve_destroy(s); return rc; }
     for (auto &R : s->res)
@@ -309,6 +475,44 @@ int fvv_serve_submit(fvv_server *s, int user, int pair, float t, int res_id, uin
     std::lock_guard<std::mutex> lk(s->mu);
     Res &R = s->res[res_id];
     s->st.submitted++;
+    if (s->nd > 0) {
+        if (R.cams.empty()) { set_error("no frames set for this resolution"); return FVV_EINVAL; }
+        // latest wins: the user's request still waiting is replaced
+        auto q = s->queued_of_user.find(user);
+        if (q != s->queued_of_user.end()) {
+            Request &old = s->reqs[q->second];
+            if (old.state == RQ_QUEUED) {
+                old.state = RQ_SUPERSEDED;
+                old.t_done = now_ms();
+                s->st.superseded++;
+            }
+            s->queued_of_user.erase(q);
+        }
+        const int full = 1 << s->cfg.dense_levels;
+        Request r;
+        r.user = user; r.pair = pair; r.res = res_id; r.t = t; r.t_submit = now_ms();
+        r.k = std::min(full, std::max(0, (int)std::lround(t * full)));
+        const uint64_t tk = s->next_ticket++;
+        if (r.k == 0 || r.k == full) {
+            // a camera: its own frame
+            r.out = R.cams[r.k == 0 ? pair : pair + 1];
+            r.state = RQ_DONE;
+            r.t_done = r.t_submit;
+            s->st.completed++;
+            s->lat.push_back(0.0);
+            s->reqs[tk] = r;
+        } else if (R.d_cur >= 0 && R.d_inst[R.d_cur] == R.frames_id) {
+            s->reqs[tk] = r;
+            dense_answer(s, s->reqs[tk], now_ms());
+        } else {
+            s->reqs[tk] = r;
+            R.d_waiting.push_back(tk);
+            s->queued_of_user[user] = tk;
+        }
+        *ticket = tk;
+        s->cv.notify_all();
+        return FVV_OK;
+    }
     // latest wins: the user's request still waiting is replaced (its buffer reused)
     int buf = -1;
     auto q = s->queued_of_user.find(user);
@@ -349,7 +553,7 @@ int fvv_serve_poll(fvv_server *s, uint64_t ticket, const float **out_dev, double
     Request &r = it->second;
     switch (r.state) {
     case RQ_DONE:
-        if (out_dev) *out_dev = r.buf >= 0 ? s->res[r.res].pool[r.buf] : nullptr;
+        if (out_dev) *out_dev = s->nd > 0 ? r.out : (r.buf >= 0 ? s->res[r.res].pool[r.buf] : nullptr);
         if (latency_ms) *latency_ms = r.t_done - r.t_submit;
         return 0;
     case RQ_SUPERSEDED: set_error("superseded by a newer request of the same user"); return FVV_ESUPERSEDED;
@@ -384,7 +588,7 @@ int fvv_serve_stats_get(fvv_server *s, fvv_serve_stats *out) {
     out->max_ms = l.empty() ? 0.0 : l.back();
     out->device_bytes = s->dev_bytes;
     out->queued = 0;
-    for (auto &R : s->res) out->queued += (long long)R.queue.size();
+    for (auto &R : s->res) out->queued += (long long)R.queue.size() + (long long)R.d_waiting.size();
     return FVV_OK;
 }
 
@@ -405,6 +609,7 @@ void fvv_serve_destroy(fvv_server *s) {
                 fvv_interp_destroy(sl.h);
             }
             for (float *p : R.pool) if (p) cudaFree(p);
+            for (float *p : R.dstore) if (p) cudaFree(p);
         }
     }
     delete s;

@@ -64,3 +64,44 @@ def test_server_mix_matches_alone():
         assert st["completed"] == 10 and st["failed"] == 0 and st["device_bytes"] > 0
     finally:
         fvv.fvv_serve_destroy(s)
+
+
+def test_dense_mode_views_match_alone():
+    """Dense mode: the per-instant view set, served by snapping t to k / 2^n, equals
+    each view computed alone at t = k / 2^n (bit for bit); a new instant's frames
+    give that instant's views."""
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    h, w = 48, 80
+    frames = [[torch.from_numpy(c).cuda() for c in scene.rig(30 + i, h, w, n_cams=3, max_disp=6.0)]
+              for i in range(2)]
+    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=1, res_h=[h], res_w=[w], n_cams=3,
+                                    slots_per_res=2, max_batch=6, dense_levels=2)
+    s = fvv.fvv_serve_create(blob(), cfg)
+    alone = fvv.Interpolator(blob(), h, w, precision=fvv.FVV_BF16, max_views=1)
+    try:
+        for inst in range(2):
+            cams = frames[inst]
+            fvv.fvv_serve_set_frames(s, inst, 0, cams)
+            for u, (p, t) in enumerate([(0, 0.3), (1, 0.5), (0, 0.8), (1, 0.05), (0, 0.97)]):
+                tk = fvv.fvv_serve_submit(s, 10 * inst + u, p, t, 0)
+                t0 = time.time()
+                while True:
+                    st, ptr, lat = fvv.fvv_serve_poll(s, tk)
+                    if st == 0:
+                        break
+                    assert time.time() - t0 < 30
+                    time.sleep(0.001)
+                got = _fetch(ptr, (h, w, 3))
+                k = min(4, max(0, round(t * 4)))
+                if k in (0, 4):
+                    ref = cams[p if k == 0 else p + 1].cpu().numpy()
+                else:
+                    ref = alone.run(cams[p], cams[p + 1], [k / 4]).cpu().numpy()[0]
+                np.testing.assert_array_equal(got, ref)
+                fvv.fvv_serve_release(s, tk)
+            st = fvv.fvv_serve_stats_get(s)
+            assert st["dense_instants"] == inst + 1 and st["failed"] == 0
+    finally:
+        fvv.fvv_serve_destroy(s)

@@ -114,3 +114,50 @@ def test_bad_requests():
             assert e.value.code == fvv.FVV_EINVAL
     finally:
         fvv.fvv_serve_destroy(s)
+
+
+def test_dense_mode_renders_once_per_instant_and_snaps():
+    # 5 cameras -> 4 pairs; n = 2 levels -> 3 views per pair (t = 1/4, 1/2, 3/4);
+    # max_batch 6 -> two pairs per render batch
+    s = _server(slots_per_res=2, max_batch=6, dense_levels=2, fake=1.0)
+    view_bytes = 64 * 64 * 3 * 4
+    cams = [0x1000 * (i + 1) for i in range(5)]
+    try:
+        fvv.fvv_serve_set_frames(s, 0, 0, cams)
+        rng = __import__("numpy").random.default_rng(4)
+        reqs = []
+        for u in range(40):                       # many users, one render
+            p, t = int(rng.integers(0, 4)), float(rng.uniform(0, 1))
+            reqs.append((fvv.fvv_serve_submit(s, u, p, t, 0), p, t))
+        for tk, p, t in reqs:
+            _wait(s, tk)
+            st, ptr, lat = fvv.fvv_serve_poll(s, tk)
+            k = min(4, max(0, round(t * 4)))
+            if k == 0:
+                assert ptr == cams[p]
+            elif k == 4:
+                assert ptr == cams[p + 1]
+            else:                                  # first store, layout [pair][k - 1]
+                assert ptr == (1 << 40) + (p * 3 + k - 1) * view_bytes
+        st = fvv.fvv_serve_stats_get(s)
+        assert st["dense_instants"] == 1 and st["batches"] == 2 and st["batched_views"] == 12
+        assert st["completed"] == 40
+        # a new instant renders into the other store; later requests are answered from it
+        fvv.fvv_serve_set_frames(s, 1, 0, cams)
+        time.sleep(0.05)
+        tk = fvv.fvv_serve_submit(s, 99, 2, 0.5, 0)
+        _wait(s, tk)
+        st2, ptr, lat = fvv.fvv_serve_poll(s, tk)
+        assert ptr == (2 << 40) + (2 * 3 + 1) * view_bytes
+        st = fvv.fvv_serve_stats_get(s)
+        assert st["dense_instants"] == 2 and st["batches"] == 4
+    finally:
+        fvv.fvv_serve_destroy(s)
+
+
+def test_dense_mode_needs_whole_pairs_per_batch():
+    cfg = fvv.fvv_serve_default_cfg(fake_ms_per_view=1.0, n_res=1, res_h=[64], res_w=[64], n_cams=5,
+                                    max_batch=4, dense_levels=3)     # 7 views per pair > 4
+    with pytest.raises(fvv.FvvError) as e:
+        fvv.fvv_serve_create(None, cfg)
+    assert e.value.code == fvv.FVV_EINVAL
