@@ -156,6 +156,24 @@ int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in
 int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in, int in_cs, int in_coff, int n,
                       int H, int W, float *out, int out_cs, int out_coff, void *stream);
 
+/* Multi-view cluster frame (the paper's multiview organizer, Sec. 3.2): the real
+ * view of one camera and the views of its neighbourhood along the arc, tiled into
+ * one frame for a tile-based encoder.
+ *   center: DEVICE, H x W x 3 float32 (the camera's real view).
+ *   side_views: HOST array of 2 * n_side DEVICE pointers (H x W x 3 float32 each), in
+ *     arc order: the left neighbour camera, the views between it and the centre,
+ *     then the views between the centre and the right neighbour, the right camera
+ *     (the paper uses n_side = 16: 15 interpolated views + the neighbour per side).
+ *   out: DEVICE, W x (H + R * H / scale) x 3 float32 with R = ceil(2 n_side / scale):
+ *     rows [0, H) = center; tile k (0 <= k < 2 n_side) = side view k downscaled by the
+ *     scale x scale box average, at rows H + (k / scale) * H / scale, columns
+ *     (k % scale) * W / scale; unused tiles are zero.
+ * Errors: FVV_ESHAPE unless 1 <= n_side <= 64 and scale divides H and W; FVV_EINVAL
+ * for NULL pointers.  Asynchronous on `stream`; allocates nothing.  This operation
+ * is the system's stitching step, not part of the view interpolation network. */
+int fvv_stitch_cluster(const float *center, const float *const *side_views, int n_side, int H, int W, int scale,
+                       float *out, void *stream);
+
 /* Synchronise the device and report whether any bounded device-side wait of
  * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */

@@ -186,3 +186,26 @@ def vinet_forward(blob, left, right, t, circ=False, dumps=False):
     if rc != 0:
         raise ValueError(f"oracle_vinet_forward failed ({rc})")
     return (out, arrs) if dumps else out
+
+
+def stitch_cluster(center, side_views, scale):
+    """Multi-view cluster frame (Sec. 3.2, multiview organizer), in float64.
+
+    The centre camera's real view at full resolution on top; below it the 2 x n_side
+    views of its neighbourhood in arc order, each reduced by the scale x scale box
+    average (the pyramid's box filter) and placed `scale` per row, row by row;
+    unused tiles are zero.  The paper fixes the idea, not the layout: this layout is
+    our reading.
+    """
+    c = np.asarray(center, np.float64)
+    H, W, _ = c.shape
+    n = len(side_views)
+    th, tw = H // scale, W // scale
+    rows = -(-n // scale)
+    out = np.zeros((H + rows * th, W, 3))
+    out[:H] = c
+    for k, v in enumerate(side_views):
+        small = np.asarray(v, np.float64).reshape(th, scale, tw, scale, 3).mean(axis=(1, 3))
+        r, q = divmod(k, scale)
+        out[H + r * th:H + (r + 1) * th, q * tw:(q + 1) * tw] = small
+    return out

@@ -65,6 +65,7 @@ def lib():
         L.fvv_layer_noalloc.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
         L.fvv_interp_profile.argtypes = [_P, ctypes.c_int]
+        L.fvv_stitch_cluster.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]
         L.fvv_interp_layer_stats.argtypes = [_P, _P, _P, _P, ctypes.c_int]
         L.fvv_interp_destroy.argtypes = [_P]
         _lib = L
@@ -182,6 +183,15 @@ def fvv_layer_noalloc(layer: int, w, b, inp, in_cs: int, in_coff: int, n: int, H
     """One layer with the caller's device weights and no device allocation (see fvv.h)."""
     _check(lib().fvv_layer_noalloc(layer, _dev(w), _dev(b), _dev(inp), in_cs, in_coff, n, H, W, _dev(out),
                                    out_cs, out_coff, _stream(stream)))
+
+
+def fvv_stitch_cluster(center, side_views, H: int, W: int, scale: int, out, stream=None):
+    """Cluster frame of one camera: centre view + 2 x n_side downscaled arc views (see fvv.h)."""
+    ptrs = (ctypes.c_void_p * len(side_views))(*[_dev(v) for v in side_views])
+    if len(side_views) % 2:
+        raise ValueError("side_views must hold 2 x n_side views")
+    _check(lib().fvv_stitch_cluster(_dev(center), ptrs, len(side_views) // 2, H, W, scale, _dev(out),
+                                    _stream(stream)))
 
 
 def fvv_interp_autotune(h: int, n_views: int, cache_path: str | None = None):
