@@ -158,18 +158,25 @@ template <int BN, int MT> struct AccCfg {
 // on a clamped tile and not stored).
 // GRP = 1 (halo, small N): one stage holds a (row tap, channel block)'s A box AND its
 // three weight slices, so the MMA thread syncs once per 3 x (row bytes / 32) MMAs.
+// HT = 1 (halo, 4-phase transposed conv): the tile is MT rows x 128 pixels of one
+// phase's input grid; per channel block ONE box of (MT + 1) rows x 129 pixels feeds the
+// phase's four taps, whose operands start 0/1 rows and 0/1 pixels into it.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0, int GRP = 0>
+          int MC = 0, int GRP = 0, int HT = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES, B_BYTES = BN * ROW_BYTES;
+    constexpr uint32_t A_BYTES = HT ? (MT + 1) * 129 * ROW_BYTES : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES),
+                       B_BYTES = BN * ROW_BYTES;
+    constexpr int HROW = HT ? 129 : 130;  // pixels per row of a halo box
+    constexpr int NB = HT ? 4 : 3;        // weight slices per halo box
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
     static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
     static_assert(!GRP || (HALO && !MC), "grouped stages run on the halo path");
+    static_assert(!HT || (HALO && !MC && !GRP), "transposed-conv halo runs on the split-ring path");
     constexpr uint32_t G_STRIDE = A_STRIDE + 3 * B_STRIDE; // grouped stage: A box + 3 weight slices
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
@@ -260,16 +267,22 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int t = blockIdx.x; t < t_end && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
                 tile_coords(p, t < p.num_tiles ? t : p.num_tiles - 1, ph, n, y0, x0);
-                for (int ky = 0; ky < 3 && !stop; ++ky)
-                    for (int c = 0; c < p.nck && !stop; ++c) {
+                // boxes in K order: (ky, channel block) for 3x3 taps, channel block for the phase's taps
+                const int ngroups = HT ? p.nck : 3 * p.nck;
+                for (int grp = 0; grp < ngroups && !stop; ++grp) {
+                        const int ky = HT ? 0 : grp / p.nck, c = HT ? grp : grp - ky * p.nck;
                         if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
                         uint32_t fa = ptx::smem_u32(&bars->full[sa]);
                         ptx::mbar_arrive_expect_tx(fa, A_BYTES);
-                        ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
-                                         y0 + ky - 1, n);
+                        if (HT) // rows y0 + dy_min .., pixels x0 + dx_min .. (dy, dx in {-1, 0} or {0, 1} by phase)
+                            ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK,
+                                             x0 - ((ph & 1) ? 0 : 1), y0 - ((ph >> 1) ? 0 : 1), n);
+                        else
+                            ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
+                                             y0 + ky - 1, n);
                         ++issued_a;
                         if (++sa == STAGES) { sa = 0; pa ^= 1; }
-                        for (int kx = 0; kx < 3; ++kx) {
+                        for (int kx = 0; kx < NB; ++kx) {
                             const int slot = STAGES + sb;
                             if (!wait_bar(ptx::smem_u32(&bars->empty[slot]), pb ^ 1, abort, p.err, 1)) { stop = true; break; }
                             uint32_t fbb = ptx::smem_u32(&bars->full[slot]);
@@ -278,11 +291,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 ptx::tma_load_3d_mc(ptx::smem_u32(sB + sb * B_STRIDE) + rank * (B_BYTES / 2), &tmB, fbb,
                                                     c * CK, (int)rank * (BN / 2), ky * 3 + kx, (uint16_t)3);
                             else
-                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
+                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0,
+                                                 HT ? ph * 4 + kx : ky * 3 + kx);
                             ++issued_b;
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
-                    }
+                }
             }
             if (MC && !*abort && !stop) {
                 // every B slot's last use released by both CTAs: no commit of either
@@ -335,6 +349,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                          y0 - (ky == 0 ? 1 : 0), n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
                     } else {
+                        // K order (channel block, tap): the same as the transposed-conv halo path
+                        tap = kb & 3;
+                        c0 = (kb >> 2) * CK;
                         int py = ph >> 1, px = ph & 1, ty = tap >> 1, tx = tap & 1;
                         int dy = py == 0 ? -ty : 1 - ty, dx = px == 0 ? -tx : 1 - tx;
                         ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + dx, y0 + dy, n);
@@ -414,12 +431,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const uint32_t d = tmem + acc * (MT * BN);
                 bool ok = true;
                 uint32_t accumulate = 0;
-                for (int ky = 0; ky < 3 && ok; ++ky)
-                    for (int c = 0; c < p.nck && ok; ++c) {
+                const int ngroups = HT ? p.nck : 3 * p.nck;
+                for (int grp = 0; grp < ngroups && ok; ++grp) {
                         if (!wait_bar(ptx::smem_u32(&bars->full[sa]), pa, abort, p.err, 3)) { ok = false; break; }
                         ptx::tc_fence_after();
                         const uint32_t a0 = ptx::smem_u32(sA + sa * A_STRIDE);
-                        for (int kx = 0; kx < 3; ++kx) {
+                        for (int kx = 0; kx < NB; ++kx) {
                             if (!wait_bar(ptx::smem_u32(&bars->full[STAGES + sb]), pb, abort, p.err, 3)) { ok = false; break; }
                             ptx::tc_fence_after();
                             const uint32_t b0 = ptx::smem_u32(sB + sb * B_STRIDE);
@@ -431,7 +448,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
 #pragma unroll
                                 for (int m = 0; m < MT; ++m) {
-                                    uint64_t ad = ptx::smem_desc(a0 + (m * 130 + kx) * ROW_BYTES + k * 32, ROW_BYTES);
+                                    // 3x3: row block m, column tap kx; transposed: tap (ty, tx) =
+                                    // (kx >> 1, kx & 1) reads box row m + 1 - ty, pixel 1 - tx on
+                                    const int row0 = HT ? (m + 1 - (kx >> 1)) * HROW + 1 - (kx & 1) : m * HROW + kx;
+                                    uint64_t ad = ptx::smem_desc(a0 + row0 * ROW_BYTES + k * 32, ROW_BYTES);
                                     if (F8) ptx::mma_f8(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
                                     else ptx::mma_bf16(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
                                 }
@@ -445,7 +465,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         if (!ok) break;
                         ptx::mma_commit(ptx::smem_u32(&bars->empty[sa]));
                         if (++sa == STAGES) { sa = 0; pa ^= 1; }
-                    }
+                }
                 if (!ok) break;
                 ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
                 if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
@@ -1005,6 +1025,54 @@ int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensor
                        : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mc, p, st);
 }
 
+// Transposed-conv halo (4-phase convT, 128-byte rows): a box of (MT + 1) x 129 pixels
+// per channel block, two A stages, the weight ring takes the rest of the budget.
+template <int BN, int TS, int MT> struct HaloTCfg {
+    static constexpr uint32_t A = ((MT + 1) * 129 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
+    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr int CTAS = BN <= 32 ? 2 : 1, STAGES = 2;
+    static constexpr int fit = (int)((kSmemBudget / CTAS - 2048 - STG - STAGES * A) / B);
+    static constexpr int STAGES_B = fit > 12 ? 12 : fit;
+    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
+    static_assert(STAGES_B >= 4 && CTAS * AccCfg<BN, MT>::TMEM_COLS <= 512, "transposed halo config");
+};
+
+template <int BN, int TS, int MT>
+int launch_halo_t(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+                  cudaStream_t st) {
+    using C = HaloTCfg<BN, TS, MT>;
+    auto kern = conv_tc_kernel<BN, 64, MT, C::STAGES, C::CTAS, 0, 1, C::STAGES_B, TS, 0, 0, 1>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+// Measured on the 1080p forward: 15% faster for N = 32 (RefineNet d2); slower for
+// N = 64 (d1, one CTA per SM) and N = 128 with two row blocks (VIB t0), which keep
+// the per-tap boxes.
+bool halo_t_ok(int bn, int ck, int es, bool f8) { return !f8 && ck * es == 128 && bn == 32; }
+
+template <int TS>
+int dispatch_halo_t_ts(int bn, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
+                       cudaStream_t st) {
+    if (bn == 32) return launch_halo_t<32, TS, 1>(ma, mb, mc, p, st);
+    set_error("no transposed-conv halo kernel for N=%d", bn);
+    return FVV_EINVAL;
+}
+
 template <int TS>
 int dispatch_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
                 const TcParams &p, cudaStream_t st) {
@@ -1178,9 +1246,13 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     }
     // default tile of the 3x3 stride-1 layers with 128-byte operand rows: one row of
     // 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
-    const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
-                      p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT);
-    const int halo_mt = bn == 256 ? kHaloMT256 : 1;
+    // the 4-phase transposed convs: one (MT + 1)-row box per channel block feeds the
+    // phase's four taps (MT = the layer's row blocks: 2 for N = 128)
+    const bool halo_t = force < 0 && p.mode == MODE_T && halo_t_ok(bn, ck, es, f8) && p.gw >= 96 &&
+                        (!epi || epi->mode == EPI_STORE);
+    const bool halo = halo_t || (force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
+                                 p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT));
+    const int halo_mt = halo_t ? mt : (bn == 256 ? kHaloMT256 : 1);
     if (halo) s = Shape{halo_mt - 1, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
@@ -1225,7 +1297,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1}; // halo: th_ = MT
+        // halo boxes: MT rows x 130 pixels (3x3), (MT + 1) rows x 129 pixels (4-phase convT)
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo_t ? tw_ + 1 : (halo ? tw_ + 2 : tw_)),
+                             (cuuint32_t)(halo_t ? th_ + 1 : th_), 1};
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
     g_encode_u8 = false;
@@ -1260,6 +1334,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             FVV_TRY(rc);
         }
     }
+    if (halo_t)
+        return p.tma_store ? dispatch_halo_t_ts<1>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st)
+                           : dispatch_halo_t_ts<0>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st);
     if (halo)
         return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half, mc, p, st);
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);

@@ -12,7 +12,8 @@ column taps read it 0, 1, 2 rows in.  Checks:
   (each loads one half and multicasts it): odd tile counts included;
 * the whole BF16 forward with the halo tiles equals, bit for bit, the same
   forward with every layer forced onto plain 1 x 128 tiles: both accumulate
-  the K loop in the order (row tap, channel block, column tap).
+  the K loop in the order (row tap, channel block, column tap), or (channel block,
+  tap) for the 4-phase transposed convs.
 """
 import json
 
@@ -26,9 +27,10 @@ from tests.gpu_common import blob, pair
 
 pytestmark = pytest.mark.gpu
 
-# 128-byte rows (C_in >= 64) and the narrow 32- / 64-byte rows (C_in = 16, 32)
+# 128-byte rows (C_in >= 64), the narrow 32- / 64-byte rows (C_in = 16, 32) and the
+# 4-phase transposed convs (one (row blocks + 1) x 129-pixel box per channel block)
 HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3", "ctx.c1", "ctx.c3",
-               "ref.e0b"]
+               "ref.e0b", "ref.d2"]
 
 
 @pytest.fixture(scope="module")
