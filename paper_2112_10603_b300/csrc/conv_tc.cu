@@ -104,7 +104,7 @@ __device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase
 }
 
 // One output element of the epilogue (scalar path): bias, ReLU, then store, or
-// the fused Eq. 2 update, or the fused residual output.
+// the fused Eq. 2 update.
 __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int ox, int co, float acc) {
     float x = acc * (p.acc_scale ? __ldg(p.acc_scale + co) : 1.f) + __ldg(p.bias + co);
     if (p.relu) x = fmaxf(x, 0.f);
@@ -117,13 +117,6 @@ __device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int o
         Taps u = up_taps(ox, oy, h2, w2, 0);
         x += bilerp(fm, 5, co, u) * (co < 4 ? 2.f : 1.f);
         ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
-    } else if (p.epi.mode == EPI_OUTPUT) {
-        // clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to the caller's H x W
-        if (oy < p.epi.crop_h && ox < p.epi.crop_w) {
-            float r = 2.f * sigmoidf_(x) - 1.f;
-            float v = fminf(fmaxf(p.epi.ib[pix * 3 + co] + r, 0.f), 1.f);
-            (*p.epi.final_out_ref)[(((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3 + co] = v;
-        }
     } else if (p.out_f32) {
         ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
     } else if (p.out_fp8) {
@@ -598,27 +591,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
                             ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
                         }
-                    }
-                }
-            } else if (MT == 1 && BN == 16 && p.epi.mode == EPI_OUTPUT) {
-                // residual output fused into the 16 -> 3 conv: I_blend fetched early
-                const bool in_crop = valid && gy < p.epi.crop_h && gx < p.epi.crop_w;
-                size_t pix = ((size_t)n * p.out_h + gy) * p.out_w + gx;
-                float ibv[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) ibv[k] = in_crop ? __ldg(p.epi.ib + pix * 3 + k) : 0.f;
-                if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
-                ptx::tc_fence_after();
-                uint32_t r[16];
-                __syncwarp();
-                ptx::tmem_ld16(tbase, r);
-                ptx::tmem_ld_wait();
-                if (in_crop) {
-                    float *dst = *p.epi.final_out_ref + (((size_t)n * p.epi.crop_h + gy) * p.epi.crop_w + gx) * 3;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        float z = __uint_as_float(r[k]) + __ldg(p.bias + k);
-                        dst[k] = fminf(fmaxf(ibv[k] + 2.f * sigmoidf_(z) - 1.f, 0.f), 1.f);
                     }
                 }
             } else {
@@ -1251,7 +1223,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     const bool halo_t = force < 0 && p.mode == MODE_T && halo_t_ok(bn, ck, es, f8) && p.gw >= 96 &&
                         (!epi || epi->mode == EPI_STORE);
     const bool halo = halo_t || (force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
-                                 p.gw >= 96 && (!epi || epi->mode != EPI_OUTPUT));
+                                 p.gw >= 96);
     const int halo_mt = halo_t ? mt : (bn == 256 ? kHaloMT256 : 1);
     if (halo) s = Shape{halo_mt - 1, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
@@ -1277,8 +1249,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them
         bool ok = (epi->mode == EPI_STORE) ||
-                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5) ||
-                  (epi->mode == EPI_OUTPUT && p.mode == MODE_S1 && L.co == 3 && bn == 16);
+                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5);
         if (!ok) { set_error("layer %s: unsupported fused epilogue", L.name); return FVV_EINVAL; }
     }
 

@@ -124,9 +124,14 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
     const LayerDef &L = kLayers[li];
     // the 16 -> 3 output conv with the fused residual output: 3 useful columns of a
     // 16-wide tensor-core tile do not pay; a tiled direct kernel does the job
-    if (is_bf16(h) && li == kRef + 12 && epi && epi->mode == EPI_OUTPUT && in_cs == 16 && in_coff == 0)
+    if (epi && epi->mode == EPI_OUTPUT) {
+        if (!is_bf16(h) || li != kRef + 12 || in_cs != 16 || in_coff != 0) {
+            set_error("the fused residual output runs on the bf16 16 -> 3 output conv only");
+            return FVV_EINVAL;
+        }
         return launch_out_conv_fused((const bf16 *)in, N, Hin, Win, h->w32 + h->w_off[li], h->bias + h->b_off[li],
                                      epi->ib, epi->final_out_ref, epi->crop_h, epi->crop_w, st);
+    }
     // ContextNet's first layer reads the 3-channel FP32 frame: SIMT on every path
     const bool simt = !is_bf16(h) || li == kCtx;
     if (!simt) return tc_conv(h, li, in, in_cs, in_coff, N, Hin, Win, out, out_cs, out_coff, out_f32, st, epi);
