@@ -95,6 +95,23 @@ int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const f
 int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t,
                         int n_views, float *out, void *stream);
 
+/* Pipelined form of fvv_interp_run_host: enqueues the copy of left/right (HOST, H x W x 3
+ * float32) to the device, the forward on `stream` and the copy of the views back into out
+ * (HOST, n_views x H x W x 3 float32), and returns without waiting; *ticket receives the
+ * call's number (0, 1, 2, ... per handle).  The copies run on the handle's own copy streams,
+ * so the copy-out of one call overlaps the forward of the next.  Two calls are in flight at
+ * most: a call first waits (host) until the call two before it has delivered its views.
+ * left, right and out stay owned by the caller and must not be touched until
+ * fvv_interp_wait_host(h, ticket) has returned; page-locked memory is needed for the
+ * copies to overlap (pageable memory works, serialised).
+ * Errors: FVV_EINVAL (NULL argument, t outside [0, 1]), FVV_ESHAPE (n_views), FVV_ECUDA. */
+int fvv_interp_submit_host(fvv_interp *h, const float *left, const float *right, const float *t,
+                           int n_views, float *out, void *stream, long long *ticket);
+
+/* Block until the host-buffer call `ticket` has written its views into its out buffer.
+ * A ticket that was never issued by this handle gives FVV_EINVAL. */
+int fvv_interp_wait_host(fvv_interp *h, long long ticket);
+
 /* Batched rig instant: n_cams frames, n_pairs camera pairs, uneven views per pair.
  * cams: HOST array of n_cams DEVICE pointers (H x W x 3 float32 each).
  * pair_left: HOST, n_pairs camera indices; pair p uses cams pair_left[p] and

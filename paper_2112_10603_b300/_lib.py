@@ -54,6 +54,9 @@ def lib():
                                         ctypes.POINTER(fvv_opts), ctypes.POINTER(_P)]
         L.fvv_interp_run.argtypes = [_P, _P, _P, _P, ctypes.c_int, _P, _P]
         L.fvv_interp_run_host.argtypes = [_P, _P, _P, _P, ctypes.c_int, _P, _P]
+        L.fvv_interp_submit_host.argtypes = [_P, _P, _P, _P, ctypes.c_int, _P, _P,
+                                             ctypes.POINTER(ctypes.c_longlong)]
+        L.fvv_interp_wait_host.argtypes = [_P, ctypes.c_longlong]
         L.fvv_interp_run_batch.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P]
         L.fvv_interp_device_bytes.argtypes = [_P]
         L.fvv_interp_device_bytes.restype = ctypes.c_size_t
@@ -146,6 +149,23 @@ def fvv_interp_run_host(h: int, left, right, t, n_views: int, out, stream=None):
     ta, tp = _host_f32(t)
     oa, op = _host_buf(out, writable=True)
     _check(lib().fvv_interp_run_host(h, lp, rp, tp, n_views, op, _stream(stream)))
+
+
+def fvv_interp_submit_host(h: int, left, right, t, n_views: int, out, stream=None) -> int:
+    """Enqueue a host-buffer call and return its ticket.  The copies run after this
+    returns, so left, right and out are used in place (float32, C-contiguous; no
+    temporary copy is made) and must stay alive until fvv_interp_wait_host."""
+    _, lp = _host_buf(left, writable=True)
+    _, rp = _host_buf(right, writable=True)
+    ta, tp = _host_f32(t)
+    _, op = _host_buf(out, writable=True)
+    tk = ctypes.c_longlong(-1)
+    _check(lib().fvv_interp_submit_host(h, lp, rp, tp, n_views, op, _stream(stream), ctypes.byref(tk)))
+    return tk.value
+
+
+def fvv_interp_wait_host(h: int, ticket: int):
+    _check(lib().fvv_interp_wait_host(h, ticket))
 
 
 def fvv_interp_run_batch(h: int, cams, pair_left, view_offsets, t, out, stream=None):

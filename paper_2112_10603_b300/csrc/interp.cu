@@ -539,24 +539,81 @@ int fvv_interp_run(fvv_interp *h, const float *left, const float *right, const f
     return dispatch_forward(h, 2, n_views, st);
 }
 
-int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
-                        float *out, void *stream) {
-    clear_error();
-    if (!h || !left || !right || !t || !out) { set_error("NULL argument"); return FVV_EINVAL; }
-    if (n_views < 1 || n_views > h->o.max_views) {
-        set_error("n_views = %d outside [1, %d]", n_views, h->o.max_views); return FVV_ESHAPE;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    size_t img = (size_t)h->H * h->W * 3;
+// Device staging and copy streams of the host-buffer calls (allocated on first use).
+static int ensure_host_slots(fvv_interp *h) {
+    const size_t img = (size_t)h->H * h->W * 3;
     if (!h->d_in) {
         FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
         FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
     }
-    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_in, left, img * 4, cudaMemcpyHostToDevice, st));
-    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_in + img, right, img * 4, cudaMemcpyHostToDevice, st));
-    FVV_TRY(fvv_interp_run(h, h->d_in, h->d_in + img, t, n_views, h->d_out, stream));
-    FVV_CHECK_CUDA(cudaMemcpyAsync(out, h->d_out, n_views * img * 4, cudaMemcpyDeviceToHost, st));
-    FVV_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (h->s_h2d) return FVV_OK;
+    h->hs[0].d_in = h->d_in;
+    h->hs[0].d_out = h->d_out;
+    FVV_TRY(dalloc_t(h, &h->hs[1].d_in, 2 * img * 4));
+    FVV_TRY(dalloc_t(h, &h->hs[1].d_out, (size_t)h->o.max_views * img * 4));
+    for (auto &sl : h->hs) {
+        FVV_CHECK_CUDA(cudaEventCreateWithFlags(&sl.in_ready, cudaEventDisableTiming));
+        FVV_CHECK_CUDA(cudaEventCreateWithFlags(&sl.fwd_done, cudaEventDisableTiming));
+        FVV_CHECK_CUDA(cudaEventCreateWithFlags(&sl.out_done, cudaEventDisableTiming));
+    }
+    FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
+    FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
+    return FVV_OK;
+}
+
+// Wait (host) until every pipelined host-buffer call has delivered its views, so that
+// slot 0's staging (shared with calibration and autotuning) is free.
+static int drain_host_slots(fvv_interp *h) {
+    if (!h->s_h2d) return FVV_OK;
+    for (auto &sl : h->hs)
+        if (sl.ticket >= 0) FVV_CHECK_CUDA(cudaEventSynchronize(sl.out_done));
+    return FVV_OK;
+}
+
+int fvv_interp_submit_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
+                           float *out, void *stream, long long *ticket) {
+    clear_error();
+    if (!h || !left || !right || !t || !out || !ticket) { set_error("NULL argument"); return FVV_EINVAL; }
+    if (n_views < 1 || n_views > h->o.max_views) {
+        set_error("n_views = %d outside [1, %d]", n_views, h->o.max_views); return FVV_ESHAPE;
+    }
+    FVV_TRY(check_t(t, n_views));
+    FVV_TRY(ensure_host_slots(h));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t img = (size_t)h->H * h->W * 3;
+    fvv_interp::HostSlot &sl = h->hs[h->host_calls & 1];
+    // the call two back used this slot: its views must be out before the staging is reused
+    if (sl.ticket >= 0) FVV_CHECK_CUDA(cudaEventSynchronize(sl.out_done));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(sl.d_in, left, img * 4, cudaMemcpyHostToDevice, h->s_h2d));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(sl.d_in + img, right, img * 4, cudaMemcpyHostToDevice, h->s_h2d));
+    FVV_CHECK_CUDA(cudaEventRecord(sl.in_ready, h->s_h2d));
+    FVV_CHECK_CUDA(cudaStreamWaitEvent(st, sl.in_ready, 0));
+    FVV_TRY(fvv_interp_run(h, sl.d_in, sl.d_in + img, t, n_views, sl.d_out, stream));
+    FVV_CHECK_CUDA(cudaEventRecord(sl.fwd_done, st));
+    FVV_CHECK_CUDA(cudaStreamWaitEvent(h->s_d2h, sl.fwd_done, 0));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(out, sl.d_out, n_views * img * 4, cudaMemcpyDeviceToHost, h->s_d2h));
+    FVV_CHECK_CUDA(cudaEventRecord(sl.out_done, h->s_d2h));
+    sl.ticket = h->host_calls;
+    *ticket = h->host_calls++;
+    return FVV_OK;
+}
+
+int fvv_interp_wait_host(fvv_interp *h, long long ticket) {
+    clear_error();
+    if (!h) { set_error("NULL handle"); return FVV_EINVAL; }
+    if (ticket < 0 || ticket >= h->host_calls) { set_error("no host-buffer call with ticket %lld", ticket); return FVV_EINVAL; }
+    const fvv_interp::HostSlot &sl = h->hs[ticket & 1];
+    // a slot reused by a later call was waited for before the reuse
+    if (sl.ticket == ticket) FVV_CHECK_CUDA(cudaEventSynchronize(sl.out_done));
+    return FVV_OK;
+}
+
+int fvv_interp_run_host(fvv_interp *h, const float *left, const float *right, const float *t, int n_views,
+                        float *out, void *stream) {
+    long long tk = -1;
+    FVV_TRY(fvv_interp_submit_host(h, left, right, t, n_views, out, stream, &tk));
+    FVV_TRY(fvv_interp_wait_host(h, tk));
+    FVV_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return FVV_OK;
 }
 
@@ -674,6 +731,7 @@ int fvv_calibrate_fp8(fvv_interp *h, const float *frames, int n_pairs, void *str
     const size_t img = (size_t)h->H * h->W * 3;
     const int nv = h->o.max_views < 3 ? h->o.max_views : 3;
     const float ts[3] = {0.25f, 0.5f, 0.75f};
+    FVV_TRY(drain_host_slots(h));
     if (!h->d_out) {
         FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
         FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
@@ -765,6 +823,7 @@ int fvv_interp_autotune(fvv_interp *h, int n_views, const char *cache_path) {
     if (cache.count(key) && apply_tune_entry(h, cache[key])) return FVV_OK;
     // frames: zeros (timing does not depend on values)
     size_t img = (size_t)h->H * h->W * 3;
+    FVV_TRY(drain_host_slots(h));
     if (!h->d_in) {
         FVV_TRY(dalloc_t(h, &h->d_in, 2 * img * 4));
         FVV_TRY(dalloc_t(h, &h->d_out, (size_t)h->o.max_views * img * 4));
@@ -834,6 +893,11 @@ void fvv_interp_destroy(fvv_interp *h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (auto &sl : h->hs)
+        for (cudaEvent_t e : {sl.in_ready, sl.fwd_done, sl.out_done})
+            if (e) cudaEventDestroy(e);
+    if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+    if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     delete h;
 }
 

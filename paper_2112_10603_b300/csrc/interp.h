@@ -62,8 +62,17 @@ struct fvv_interp {
     const float **d_cams = nullptr;
     char *h_stage = nullptr;
     cudaEvent_t stage_done = nullptr;
-    // staging for host-buffer calls
+    // staging for host-buffer calls: slot 0 is d_in/d_out; the pipelined calls alternate
+    // between two slots, copies on their own streams so a copy-out overlaps the next forward
     float *d_in = nullptr, *d_out = nullptr;
+    struct HostSlot {
+        float *d_in = nullptr, *d_out = nullptr;
+        cudaEvent_t in_ready = nullptr, fwd_done = nullptr, out_done = nullptr;
+        long long ticket = -1; // the call that used the slot last
+    };
+    HostSlot hs[2];
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    long long host_calls = 0;
     int *d_err = nullptr; // device error word written by bounded waits
     size_t dev_bytes = 0;
     int last_launches = 0;

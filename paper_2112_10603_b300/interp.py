@@ -30,6 +30,15 @@ class Interpolator:
         L.fvv_interp_run_host(self.h, left, right, t, len(t), out, None)
         return out
 
+    def submit_host(self, left, right, t, out):
+        """Pipelined host-buffer call: returns a ticket for wait_host.  left, right, out:
+        float32 host buffers (pinned tensors for overlap) kept alive until the wait."""
+        t = np.atleast_1d(np.asarray(t, np.float32))
+        return L.fvv_interp_submit_host(self.h, left, right, t, len(t), out, None)
+
+    def wait_host(self, ticket: int):
+        L.fvv_interp_wait_host(self.h, ticket)
+
     def run_batch(self, cams, pair_left, view_offsets, t, out=None, stream=None):
         import torch
         t = np.asarray(t, np.float32)

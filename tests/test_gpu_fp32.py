@@ -87,6 +87,40 @@ def test_batch_invariance_and_host_path(torch_cuda):
     np.testing.assert_array_equal(host, many)
 
 
+def test_pipelined_host_calls(torch_cuda):
+    """Two host-buffer calls in flight (the copy-out of one overlapping the forward of
+    the next), distinct inputs and view sets per call, pinned and pageable buffers: each
+    call delivers exactly what the device-buffer call gives for its inputs."""
+    torch = torch_cuda
+    H, W = 48, 80
+    it = _interp(H, W, max_views=3)
+    calls = []
+    for k in range(5):
+        left, right = pair(30 + k, H, W, 6.0)
+        ts = [0.1 * (k + 1), 0.95][: 1 + k % 2]
+        if k % 2:
+            lh, rh = torch.from_numpy(left).pin_memory(), torch.from_numpy(right).pin_memory()
+            out = torch.full((len(ts), H, W, 3), -1.0).pin_memory()
+        else:
+            lh, rh, out = left, right, np.full((len(ts), H, W, 3), -1.0, np.float32)
+        calls.append((left, right, ts, lh, rh, out))
+    tickets = []
+    for k, (_, _, ts, lh, rh, out) in enumerate(calls):
+        tickets.append(it.submit_host(lh, rh, ts, out))
+        if k:
+            it.wait_host(tickets[k - 1])
+    it.wait_host(tickets[-1])
+    it.wait_host(tickets[0])          # long done: returns at once
+    assert tickets == list(range(tickets[0], tickets[0] + 5))
+    for left, right, ts, _, _, out in calls:
+        want = it.run(_dev(torch, left), _dev(torch, right), ts).cpu().numpy()
+        got = out.numpy() if hasattr(out, "numpy") else out
+        np.testing.assert_array_equal(got, want)
+    with pytest.raises(fvv.FvvError):
+        it.wait_host(tickets[-1] + 1)
+    fvv.fvv_interp_status(it.h)
+
+
 def test_run_batch_matches_per_pair_runs(torch_cuda):
     torch = torch_cuda
     from synth import scene
