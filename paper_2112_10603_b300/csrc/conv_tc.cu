@@ -168,9 +168,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
     static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
-    static_assert(!GRP || (HALO && !MC), "grouped stages run on the halo path");
+    // (BN % 8 == 0: each weight slice of a grouped box starts on a swizzle-pattern boundary)
+    static_assert(!GRP || (HALO && !MC && BN % 8 == 0), "grouped stages run on the halo path");
     static_assert(!HT || (HALO && !MC && !GRP), "transposed-conv halo runs on the split-ring path");
-    constexpr uint32_t G_STRIDE = A_STRIDE + 3 * B_STRIDE; // grouped stage: A box + 3 weight slices
+    // grouped stage: A box + the row tap's 3 weight slices, loaded as ONE box of 3 taps
+    // (slice kx at kx * B_BYTES; every B_BYTES here is a multiple of the swizzle atom)
+    constexpr uint32_t G_STRIDE = A_STRIDE + ((3 * B_BYTES + 1023) & ~1023u);
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -236,9 +239,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         ptx::mbar_arrive_expect_tx(fs, A_BYTES + 3 * B_BYTES);
                         const uint32_t base = ptx::smem_u32(sA + s * G_STRIDE);
                         ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx)
-                            ptx::tma_load_3d(base + A_STRIDE + kx * B_STRIDE, &tmB, fs, c * CK, 0, ky * 3 + kx);
+                        ptx::tma_load_3d(base + A_STRIDE, &tmB, fs, c * CK, 0, ky * 3); // taps ky*3 .. ky*3+2
                         ++issued;
                         if (++s == STAGES) { s = 0; ph_bit ^= 1; }
                     }
@@ -386,7 +387,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const uint32_t a0 = ptx::smem_u32(sA + s * G_STRIDE);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx) {
-                        const uint32_t b0 = a0 + A_STRIDE + kx * B_STRIDE;
+                        const uint32_t b0 = a0 + A_STRIDE + kx * B_BYTES;
 #pragma unroll
                         for (int k = 0; k < ROW_BYTES / 32; ++k) {
                             uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
@@ -888,7 +889,7 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
 // (measured 3-18% faster than split A/B rings; the 64-column convs with the
 // TMA-store epilogue keep split rings, which fit two CTAs per SM).
 template <int BN, int CK, int TS> struct HaloGrpCfg {
-    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, B = ((BN * CK * 2) + 1023) & ~1023u, G = A + 3 * B;
+    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, G = A + ((3 * BN * CK * 2 + 1023) & ~1023u);
     static constexpr uint32_t STG = stg_bytes(BN, TS);
     static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / G); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 2 ? ctas_for(c - 1) : c; }
@@ -976,15 +977,16 @@ bool halo_ok(int bn, int ck, int es, bool f8) {
 }
 
 // N = 256 runs as cluster pairs sharing the weight slices (mb_half: box of 128 rows)
+// (mb3: box of 3 taps, for the grouped stages)
 template <int TS>
 int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
-                     const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
+                     const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
     if (f8) return launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
-    if (ck == 16) return launch_halo_grp<16, 16, TS>(ma, mb, mc, p, st);
-    if (ck == 32) return launch_halo_grp<32, 32, TS>(ma, mb, mc, p, st);
+    if (ck == 16) return launch_halo_grp<16, 16, TS>(ma, mb3, mc, p, st);
+    if (ck == 32) return launch_halo_grp<32, 32, TS>(ma, mb3, mc, p, st);
     switch (bn) {
-    case 32: return launch_halo_grp<32, 64, TS>(ma, mb, mc, p, st);
-    case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb, mc, p, st)
+    case 32: return launch_halo_grp<32, 64, TS>(ma, mb3, mc, p, st);
+    case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb3, mc, p, st)
                                              : launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
     case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
     default: return launch_halo<256, 0, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
@@ -992,9 +994,9 @@ int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUten
 }
 
 int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
-                  const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
-    return p.tma_store ? dispatch_halo_ts<1>(bn, ck, f8, ma, mb, mb_half, mc, p, st)
-                       : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mc, p, st);
+                  const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
+    return p.tma_store ? dispatch_halo_ts<1>(bn, ck, f8, ma, mb, mb_half, mb3, mc, p, st)
+                       : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mb3, mc, p, st);
 }
 
 // Transposed-conv halo (4-phase convT, 128-byte rows): a box of (MT + 1) x 129 pixels
@@ -1135,6 +1137,11 @@ int tc_prepare(fvv_interp *h, const float *blob) {
         cuuint32_t box[3] = {(cuuint32_t)ck, (cuuint32_t)cop, 1};
         static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
         FVV_TRY(encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, ck * 2));
+        if (taps == 9) { // three consecutive taps (one row tap's column taps) per box
+            box[2] = 3;
+            FVV_TRY(encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, ck * 2));
+            box[2] = 1;
+        }
         if (cop == 256) {
             box[1] = (cuuint32_t)(cop / 2);
             FVV_TRY(encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, ck * 2));
@@ -1309,7 +1316,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         return p.tma_store ? dispatch_halo_t_ts<1>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st)
                            : dispatch_halo_t_ts<0>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st);
     if (halo)
-        return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half, mc, p, st);
+        return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half,
+                             *(const CUtensorMap *)tw.map3, mc, p, st);
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
 }
 

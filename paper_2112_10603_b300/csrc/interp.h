@@ -36,6 +36,7 @@ struct TcWeights {
     float *scale = nullptr; // FP8: per-output-channel dequantisation scale
     alignas(64) unsigned char map[128] = {}; // host CUtensorMap of w (B operand)
     alignas(64) unsigned char map_half[128] = {}; // same, box of C_out / 2 rows (cluster-pair loads)
+    alignas(64) unsigned char map3[128] = {};     // same, box of 3 consecutive taps (grouped halo stages)
     int ci_pad = 0, co_pad = 0;
 };
 
