@@ -154,14 +154,23 @@ template <int BN, int MT> struct AccCfg {
 // HT = 1 (halo, 4-phase transposed conv): the tile is MT rows x 128 pixels of one
 // phase's input grid; per channel block ONE box of (MT + 1) rows x 129 pixels feeds the
 // phase's four taps, whose operands start 0/1 rows and 0/1 pixels into it.
+// S2H = 1 (stride-2 3x3 conv whose input pixel is one channel block of 16 or 32 channels):
+// the tile is one row of 128 output pixels; per row tap ky ONE box of 129 pixel PAIRS
+// (the 5-D pair view, pair rows of 64 or 128 bytes) feeds the three column taps: kx = 1
+// reads the even pixel of pairs 1..128, kx = 0 / 2 the odd pixel of pairs 0..127 / 1..128
+// (descriptor start +1 row and/or + one pixel's bytes).  The nine weight slices stay
+// resident in shared memory (loaded once per CTA).  K order (ky, kx, k) as on the
+// per-tap path.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0, int GRP = 0, int HT = 0>
+          int MC = 0, int GRP = 0, int HT = 0, int S2H = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = HT ? (MT + 1) * 129 * ROW_BYTES : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES),
+    constexpr uint32_t A_BYTES = S2H ? 129 * 2 * ROW_BYTES
+                                     : (HT ? (MT + 1) * 129 * ROW_BYTES
+                                           : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES)),
                        B_BYTES = BN * ROW_BYTES;
     constexpr int HROW = HT ? 129 : 130;  // pixels per row of a halo box
     constexpr int NB = HT ? 4 : 3;        // weight slices per halo box
@@ -171,6 +180,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // (BN % 8 == 0: each weight slice of a grouped box starts on a swizzle-pattern boundary)
     static_assert(!GRP || (HALO && !MC && BN % 8 == 0), "grouped stages run on the halo path");
     static_assert(!HT || (HALO && !MC && !GRP), "transposed-conv halo runs on the split-ring path");
+    static_assert(!S2H || (!HALO && !MC && !GRP && !HT && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
+                           (ROW_BYTES == 32 || ROW_BYTES == 64)),
+                  "stride-2 pair halo: one 16/32-channel block, pair rows of 64/128 bytes");
+    constexpr uint32_t BR_STRIDE = (9 * B_BYTES + 1023) & ~1023u; // S2H: the resident weight slices
     // grouped stage: A box + the row tap's 3 weight slices, loaded as ONE box of 3 taps
     // (slice kx at kx * B_BYTES; every B_BYTES here is a multiple of the swizzle atom)
     constexpr uint32_t G_STRIDE = A_STRIDE + ((3 * B_BYTES + 1023) & ~1023u);
@@ -184,7 +197,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t *sB = smem + STAGES * (GRP ? G_STRIDE : A_STRIDE);
     // epilogue staging: per epilogue warp two buffers of 32 rows x STG_ROW bytes
     constexpr uint32_t STG_ROW = BN * 2 < 128 ? BN * 2 : 128, STG_BYTES = 32 * STG_ROW;
-    uint8_t *stg = sB + (GRP ? 0 : (HALO ? STAGES_B : STAGES)) * B_STRIDE;
+    uint8_t *stg = sB + (GRP ? 0u : (S2H ? BR_STRIDE : (HALO ? STAGES_B : STAGES) * B_STRIDE));
     Bars *bars = (Bars *)(stg + (TS ? 8 * STG_BYTES : 0));
     volatile int *abort = &bars->abort;
 
@@ -192,7 +205,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         // halo: full/empty[0, STAGES) = A ring, [STAGES, STAGES + STAGES_B) = B ring
-        for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES); ++s) {
+        // S2H: full[STAGES] = the resident weights
+        for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES + S2H); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), MC && s >= STAGES ? 2 : 1);
         }
@@ -224,7 +238,43 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0 && GRP) {
+        if (lane == 0 && S2H) {
+            const uint32_t fw = ptx::smem_u32(&bars->full[STAGES]);
+            ptx::mbar_arrive_expect_tx(fw, 9 * B_BYTES);
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) // taps 3ky .. 3ky + 2 per box
+                ptx::tma_load_3d(ptx::smem_u32(sB) + ky * 3 * B_BYTES, &tmB, fw, 0, 0, ky * 3);
+            int s = 0;
+            uint32_t ph_bit = 0;
+            long long issued = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+                int ph, n, y0, x0;
+                tile_coords(p, t, ph, n, y0, x0);
+                for (int ky = 0; ky < 3; ++ky) {
+                    if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
+                    const uint32_t fs = ptx::smem_u32(&bars->full[s]);
+                    ptx::mbar_arrive_expect_tx(fs, A_BYTES);
+                    // input row 2 y0 + ky - 1 = (row pair, parity) (y0 - 1, 1), (y0, 0), (y0, 1);
+                    // pairs x0 - 1 .. x0 + 127 (both pixels of each)
+                    ptx::tma_load_5d(ptx::smem_u32(sA + s * A_STRIDE), &tmA, fs, 0, x0 - 1, ky != 1 ? 1 : 0,
+                                     y0 - (ky == 0 ? 1 : 0), n);
+                    ++issued;
+                    if (++s == STAGES) { s = 0; ph_bit ^= 1; }
+                }
+            }
+            if (*abort || stop) {
+                // let every copy still in flight land before the CTA exits
+                long long t0 = clock64();
+                while (!ptx::mbar_try_wait(fw, 0) && clock64() - t0 < kWaitCycles) {}
+                for (int i = 0; i < STAGES && i < issued; ++i) {
+                    long long k = issued - 1 - i;
+                    t0 = clock64();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full[k % STAGES]), (uint32_t)((k / STAGES) & 1)) &&
+                           clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        } else if (lane == 0 && GRP) {
             int s = 0;
             uint32_t ph_bit = 0;
             long long issued = 0;
@@ -369,7 +419,50 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0 && GRP) {
+        if (lane == 0 && S2H) {
+            int s = 0;
+            uint32_t ph_bit = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool issued_any = false;
+            bool ok = wait_bar(ptx::smem_u32(&bars->full[STAGES]), 0, abort, p.err, 3); // resident weights
+            ptx::tc_fence_after();
+            const uint32_t bw = ptx::smem_u32(sB);
+            for (int t = blockIdx.x; ok && t < p.num_tiles && !*abort; t += gridDim.x) {
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem + acc * BN;
+                for (int ky = 0; ky < 3; ++ky) {
+                    if (!wait_bar(ptx::smem_u32(&bars->full[s]), ph_bit, abort, p.err, 3)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t a0 = ptx::smem_u32(sA + s * A_STRIDE);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const uint32_t b0 = bw + (ky * 3 + kx) * B_BYTES;
+                        // output pixel j reads input pixel 2j + kx - 1: pair j + (kx == 0 ? 0 : 1) of the
+                        // box, odd pixel (second ROW_BYTES of the pair row) unless kx == 1
+                        const uint32_t ak = a0 + (kx == 0 ? 0u : 2u * ROW_BYTES) + (kx == 1 ? 0u : (uint32_t)ROW_BYTES);
+#pragma unroll
+                        for (int k = 0; k < ROW_BYTES / 32; ++k) {
+                            const uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
+                            const uint64_t ad = ptx::smem_desc(ak + k * 32, 2 * ROW_BYTES);
+                            ptx::mma_bf16(d, ad, bd, IDESC, (ky | kx | k) != 0);
+                        }
+                    }
+                    issued_any = true;
+                    ptx::mma_commit(ptx::smem_u32(&bars->empty[s]));
+                    if (++s == STAGES) { s = 0; ph_bit ^= 1; }
+                }
+                if (!ok) break;
+                ptx::mma_commit(ptx::smem_u32(&bars->tmem_full[acc]));
+                if (++acc == ACCB) { acc = 0; acc_phase ^= 1; }
+            }
+            if (*abort && issued_any) {
+                ptx::mma_commit(ptx::smem_u32(&bars->drain));
+                long long t0 = clock64();
+                while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->drain), 0) && clock64() - t0 < kWaitCycles) {}
+            }
+        } else if (lane == 0 && GRP) {
             int s = 0;
             uint32_t ph_bit = 0;
             int acc = 0;
@@ -604,6 +697,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // (rows outside the output are clipped by the tensor map).  bf16 or E4M3.
             const int oes = p.out_fp8 ? 1 : 2;
             const int chb = BN * oes < 128 ? BN * oes : 128, chn = chb / oes;
+            // chn = min(BN, 64) (bf16) or min(BN, 128) (E4M3) columns per chunk: a multiple of 16 * LDB
+            constexpr int LDB = BN >= 64 ? (CTAS <= 2 ? 4 : 2) : (BN == 32 ? 2 : 1);
             const uint32_t swm = chb == 128 ? 7u : (chb == 64 ? 3u : 1u);
 #pragma unroll 1
             for (int m = 0; m < MT; ++m) {
@@ -619,11 +714,17 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     __syncwarp();
                     const uint32_t sbuf = stg_warp + (scnt & 1) * STG_BYTES;
 #pragma unroll 1
-                    for (int c = k0; c < k0 + chn; c += 16) {
-                        uint32_t r[16];
+                    for (int cb = k0; cb < k0 + chn; cb += 16 * LDB) {
+                        // LDB accumulator loads in flight per wait (their latency overlaps)
+                        uint32_t rr[LDB][16];
                         __syncwarp();
-                        ptx::tmem_ld16(tb + c, r);
+#pragma unroll
+                        for (int u = 0; u < LDB; ++u) ptx::tmem_ld16(tb + cb + 16 * u, rr[u]);
                         ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int u = 0; u < LDB; ++u) {
+                        const int c = cb + 16 * u;
+                        const uint32_t(&r)[16] = rr[u];
                         float v[16];
                         float vmax = 0.f;
 #pragma unroll
@@ -652,6 +753,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             const uint32_t a1 = a0 + 16;
                             ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), w0);
                             ptx::st_shared_v4(a1 ^ (((a1 >> 7) & swm) << 4), w1);
+                        }
                         }
                     }
                     ptx::fence_proxy_async_smem();
@@ -999,6 +1101,59 @@ int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensor
                        : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mb3, mc, p, st);
 }
 
+// Stride-2 pair halo: an A ring of 129-pair boxes, the nine weight slices resident.
+// As many CTAs per SM as keep at least four A stages.
+template <int BN, int CK, int TS> struct S2hCfg {
+    static constexpr int A = (129 * 4 * CK + 1023) & ~1023, BR = (9 * BN * CK * 2 + 1023) & ~1023;
+    static constexpr int STG = (int)stg_bytes(BN, TS);
+    static constexpr int TMEM_COLS = (int)AccCfg<BN, 1>::TMEM_COLS;
+    static constexpr int stages_for(int c) { return ((int)kSmemBudget / c - 2048 - STG - BR) / A; }
+    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
+    static constexpr int CTAS = ctas_for(512 / TMEM_COLS < 4 ? 512 / TMEM_COLS : 4);
+    static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
+    static constexpr size_t SMEM = (size_t)STAGES * A + BR + STG + sizeof(Bars) + 1024;
+    static_assert(STAGES >= 3 && CTAS * TMEM_COLS <= 512, "stride-2 halo config");
+};
+
+template <int BN, int CK, int TS>
+int launch_s2h(const CUtensorMap &ma, const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p,
+               cudaStream_t st) {
+    using C = S2hCfg<BN, CK, TS>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 0, C::STAGES, TS, 0, 0, 0, 1>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb3, mc, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+// (N tile, channel block) pairs with a stride-2 pair-halo kernel: VIB0's input conv
+// (16 channels -> 128), RefineNet e0a and ContextNet c2 (16 -> 32), c4 (32 -> 64).  The
+// 32 -> 128 VIB input convs keep the per-tap tiles: their 72 KB of resident weights
+// leave room for one CTA per SM, measured 8% slower at 1080p (VIB2 c0 483 -> 525 us).
+bool s2h_ok(int bn, int ck) { return (bn == 128 && ck == 16) || (bn == 32 && ck == 16) || (bn == 64 && ck == 32); }
+
+template <int TS>
+int dispatch_s2h_ts(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb3, const CUtensorMap &mc,
+                    const TcParams &p, cudaStream_t st) {
+    if (bn == 128 && ck == 16) return launch_s2h<128, 16, TS>(ma, mb3, mc, p, st);
+    if (bn == 32 && ck == 16) return launch_s2h<32, 16, TS>(ma, mb3, mc, p, st);
+    if (bn == 64 && ck == 32) return launch_s2h<64, 32, TS>(ma, mb3, mc, p, st);
+    set_error("no stride-2 halo kernel for N=%d, CK=%d", bn, ck);
+    return FVV_EINVAL;
+}
+
 // Transposed-conv halo (4-phase convT, 128-byte rows): a box of (MT + 1) x 129 pixels
 // per channel block, two A stages, the weight ring takes the rest of the budget.
 template <int BN, int TS, int MT> struct HaloTCfg {
@@ -1231,8 +1386,13 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
                         (!epi || epi->mode == EPI_STORE);
     const bool halo = halo_t || (force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
                                  p.gw >= 96);
+    // stride-2 layers whose input pixel is exactly one 16/32-channel block: one row of 128
+    // output pixels, one box of 129 pixel pairs per row tap, resident weights
+    const bool s2h = force < 0 && p.mode == MODE_S2 && !f8 && cip == ck && in_cs == cip && in_coff == 0 &&
+                     s2h_ok(bn, ck) && p.gw >= 96 && (!epi || epi->mode == EPI_STORE);
     const int halo_mt = halo_t ? mt : (bn == 256 ? kHaloMT256 : 1);
     if (halo) s = Shape{halo_mt - 1, 7};
+    if (s2h) s = Shape{0, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
@@ -1270,8 +1430,13 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         cuuint64_t dims[5] = {(cuuint64_t)2 * in_cs, (cuuint64_t)Win / 2, 2, (cuuint64_t)Hin / 2, (cuuint64_t)N};
         cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * e, (cuuint64_t)Win * in_cs * e,
                                  (cuuint64_t)2 * Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)tw_, 1, (cuuint32_t)th_, 1};
-        rc = encode(&ma, 5, (void *)in, dims, strides, box, ck * es);
+        if (s2h) { // 129 whole pixel pairs (2 x ck channels) of one input row
+            cuuint32_t box[5] = {(cuuint32_t)(2 * ck), 129, 1, 1, 1};
+            rc = encode(&ma, 5, (void *)in, dims, strides, box, 2 * ck * es);
+        } else {
+            cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)tw_, 1, (cuuint32_t)th_, 1};
+            rc = encode(&ma, 5, (void *)in, dims, strides, box, ck * es);
+        }
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
@@ -1312,6 +1477,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             FVV_TRY(rc);
         }
     }
+    if (s2h)
+        return p.tma_store ? dispatch_s2h_ts<1>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st)
+                           : dispatch_s2h_ts<0>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st);
     if (halo_t)
         return p.tma_store ? dispatch_halo_t_ts<1>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st)
                            : dispatch_halo_t_ts<0>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st);

@@ -10,6 +10,8 @@ column taps read it 0, 1, 2 rows in.  Checks:
   bf16-rounded input and weights, the bar of the per-layer tests;
 * the 256-channel layers run as clusters of two CTAs sharing each weight slice
   (each loads one half and multicasts it): odd tile counts included;
+* the stride-2 convs with 16/32-channel input pixels (one box of 129 pixel pairs per
+  row tap, resident weights) on ragged grids against the oracle;
 * the whole BF16 forward with the halo tiles equals, bit for bit, the same
   forward with every layer forced onto plain 1 x 128 tiles: both accumulate
   the K loop in the order (row tap, channel block, column tap), or (channel block,
@@ -85,9 +87,48 @@ def test_halo_layer_matches_oracle(torch_cuda, name):
         assert err <= 1e-4 * scale, (name, i, err, scale)
 
 
+# stride-2 convs whose input pixel is one 16- or 32-channel block: one box of 129 pixel
+# pairs per row tap feeds the three column taps, weights resident in shared memory
+# (vib2.c0, 32 -> 128, keeps the per-tap tiles: the same wide ragged grid on that path)
+S2H_LAYERS = ["vib0.c0", "ref.e0a", "ctx.c2", "ctx.c4", "vib2.c0"]
+
+
+@pytest.mark.parametrize("name", S2H_LAYERS)
+def test_stride2_pair_halo_layer_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    names = [m[0] for m in weights.manifest()]
+    li = names.index(name)
+    _, kind, ci, co, stride, relu = weights.manifest()[li]
+    assert stride == 2 and kind == "conv"
+    rng = np.random.default_rng(500 + li)
+    # output grid 3 x 132 = one full and one ragged 128-pixel tile per row; the input
+    # pixel stride is the padded channel block (16 or 32), its pad channels zero
+    H, W, n = 6, 264, 2
+    cs = 16 if ci <= 16 else 32
+    x = np.zeros((n, H, W, cs), np.float32)
+    x[..., :ci] = rng.standard_normal((n, H, W, ci)) * 0.5
+    x = _bf16_round(torch, x)
+    wv, bv = weights.layer_views(blob())[name]
+    wq = _bf16_round(torch, wv)
+    it = fvv.Interpolator(blob(), 64, 64, precision=fvv.FVV_BF16, max_views=1)
+    Ho, Wo = H // 2, W // 2
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    out = torch.full((n, Ho, Wo, co + 3), -7.0, dtype=torch.float32, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, cs, 0, n, H, W, out, co + 3, 2, True)
+    fvv.fvv_interp_status(it.h)
+    got = out.cpu().numpy()
+    assert (got[..., :2] == -7).all() and (got[..., 2 + co:] == -7).all(), "wrote outside its channel slot"
+    for i in range(n):
+        ref = oracle.conv3x3(x[i, ..., :ci], wq, bv, stride=2, relu=relu)
+        scale = max(1.0, float(np.abs(ref).max()))
+        err = np.abs(got[i, ..., 2:2 + co] - ref).max()
+        assert err <= 1e-4 * scale, (name, i, err, scale)
+
+
 def test_halo_network_bitwise_plain_tiles(torch_cuda, tmp_path):
     torch = torch_cuda
-    # 64 x 512: VIB2's 256-channel convs, vib2.t1, ref.e1b and ref.d3 take halo tiles
+    # 64 x 512: VIB2's 256-channel convs, vib2.t1, ref.e1b and ref.d3 take halo tiles;
+    # RefineNet e0a and ContextNet c2 take stride-2 pair-halo tiles
     H, W = 64, 512
     left, right = pair(21, H, W, 10.0)
     L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
