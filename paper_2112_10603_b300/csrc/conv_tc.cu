@@ -197,8 +197,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t *sB = smem + STAGES * (GRP ? G_STRIDE : A_STRIDE);
     // epilogue staging: per epilogue warp two buffers of 32 rows x STG_ROW bytes
     constexpr uint32_t STG_ROW = BN * 2 < 128 ? BN * 2 : 128, STG_BYTES = 32 * STG_ROW;
+    // staging buffers per epilogue warp: two (a chunk is staged while the previous one's
+    // store reads), one for the two-row-block tiles, whose operand stages are larger
+    constexpr int NSB = MT == 2 ? 1 : 2;
     uint8_t *stg = sB + (GRP ? 0u : (S2H ? BR_STRIDE : (HALO ? STAGES_B : STAGES) * B_STRIDE));
-    Bars *bars = (Bars *)(stg + (TS ? 8 * STG_BYTES : 0));
+    Bars *bars = (Bars *)(stg + (TS ? 4 * NSB * STG_BYTES : 0));
     volatile int *abort = &bars->abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -608,8 +611,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int row = q * 32 + lane;    // tile row = accumulator lane
         int acc = 0;
         uint32_t acc_phase = 0;
-        uint32_t scnt = 0;                // staged chunks of this warp (buffer = scnt & 1)
-        const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * 2 * STG_BYTES);
+        uint32_t scnt = 0;                // staged chunks of this warp (buffer = scnt % NSB)
+        const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * NSB * STG_BYTES);
         const int tw = 1 << p.tw_log;
         const int dy = row >> p.tw_log, dx = row & (tw - 1);
         for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
@@ -710,9 +713,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll 1
                 for (int k0 = 0; k0 < BN; k0 += chn) {
                     // the buffer staged two chunks ago must have been read by its store
-                    if (lane == 0) ptx::bulk_wait_read<1>();
+                    // the buffer's previous store (NSB chunks ago) must have been read
+                    if (lane == 0) ptx::bulk_wait_read<NSB - 1>();
                     __syncwarp();
-                    const uint32_t sbuf = stg_warp + (scnt & 1) * STG_BYTES;
+                    const uint32_t sbuf = stg_warp + (scnt % NSB) * STG_BYTES;
 #pragma unroll 1
                     for (int cb = k0; cb < k0 + chn; cb += 16 * LDB) {
                         // LDB accumulator loads in flight per wait (their latency overlaps)
@@ -924,11 +928,14 @@ int mt_for(int bn, int ck) { return ck == 64 && bn == 128 ? 2 : 1; }
 // it), so more TMA copies are in flight per SM: those layers are bound by copy latency.
 constexpr uint32_t kSmemBudget = 220 * 1024; // per SM, for all resident CTAs
 // TS = 1 adds the epilogue's staging buffers (4 warps x 2 x 32 rows).
-constexpr uint32_t stg_bytes(int bn, int ts) { return ts ? 8u * 32u * (bn * 2 < 128 ? bn * 2 : 128) : 0u; }
+// (4 warps x NSB buffers x 32 rows; NSB = 1 for two row blocks per tile)
+constexpr uint32_t stg_bytes(int bn, int ts, int mt = 1) {
+    return ts ? (mt == 2 ? 4u : 8u) * 32u * (bn * 2 < 128 ? bn * 2 : 128) : 0u;
+}
 template <int BN, int CK, int MT, int F8 = 0, int TS = 0> struct Cfg {
     static constexpr uint32_t ES = F8 ? 1 : 2;
     static constexpr uint32_t A = ((128 * MT * CK * ES) + 1023) & ~1023u, B = ((BN * CK * ES) + 1023) & ~1023u;
-    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr uint32_t STG = stg_bytes(BN, TS, MT);
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / (A + B)); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 3 + !TS ? ctas_for(c - 1) : c; }
@@ -971,7 +978,7 @@ int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &
 // two accumulators fill TMEM, so the epilogue is not overlapped with the next tile.
 template <int BN, int TS, int MT = 1> struct HaloCfg {
     static constexpr uint32_t A = (130 * MT * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
-    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr uint32_t STG = stg_bytes(BN, TS, MT);
     static constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     static constexpr int CTAS = BN >= 256 ? 1 : (BN >= 64 || TS ? 2 : 3);
     // N = 256: one A box feeds 3 weight slices (~0.8 us of MMA), so two A stages
@@ -1158,7 +1165,7 @@ int dispatch_s2h_ts(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb
 // per channel block, two A stages, the weight ring takes the rest of the budget.
 template <int BN, int TS, int MT> struct HaloTCfg {
     static constexpr uint32_t A = ((MT + 1) * 129 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
-    static constexpr uint32_t STG = stg_bytes(BN, TS);
+    static constexpr uint32_t STG = stg_bytes(BN, TS, MT);
     static constexpr int CTAS = BN <= 32 ? 2 : 1, STAGES = 2;
     static constexpr int fit = (int)((kSmemBudget / CTAS - 2048 - STG - STAGES * A) / B);
     static constexpr int STAGES_B = fit > 12 ? 12 : fit;
