@@ -123,15 +123,18 @@ __global__ void vib0_input_kernel(const float4 *img2, const ViewTab vt, int nv, 
 
 // a3: stage s input [I_l, I_r, W_l, W_r, M_up, F_up(4), t] (18 ch, zero-padded to cs)
 // at the stage grid h x w, from the previous stage's flow/mask FMp (h/2 x w/2 x 5).
+// One thread per pixel walks the views: views of one camera pair gather the same
+// image neighbourhoods, which then come from L1/L2 instead of DRAM once per view.
 template <typename T>
 __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *x, int cs) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long P = (long long)h * w;
-    if (idx >= (long long)nv * P) return;
-    int v = idx / P;
-    int p = idx % P;
-    int X = p % w, Y = p / w;
+    const long long P = (long long)h * w;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= P) return;
+    const int p = (int)pix;
+    const int X = p % w, Y = p / w;
+    for (int v = 0; v < nv; ++v) {
+    const long long idx = v * P + p;
     const float *fm = FMp + (size_t)v * (P / 4) * 5;
     Taps u = up_taps(X, Y, h / 2, w / 2, circ);
     float up[5];
@@ -151,6 +154,7 @@ __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const V
     for (int c = 0; c < 4; ++c) vals[13 + c] = up[c];
     vals[17] = vt.t[v];
     store_px(x + (size_t)idx * cs, vals, cs);
+    }
 }
 
 // Eq. 2: F^s, M^s = up(F^{s-1}) x2, up(M^{s-1}) + Res^s  (in place on res).
@@ -170,15 +174,17 @@ __global__ void residual_kernel(const float *FMp, float *res, int nv, int h, int
 
 // a5 (Eq. 1): I_l->m, I_r->m by the final flows, M = sigmoid(logit), blend.
 // Writes the refinement input [I_l->m, I_r->m] (zero-padded to cs) and I_blend.
+// One thread per pixel walks the views (image taps shared across views stay in cache).
 template <typename T>
 __global__ void final_blend_kernel(const float4 *img0, const float *FM, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *u0, int cs, float *ib) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long P = (long long)h * w;
-    if (idx >= (long long)nv * P) return;
-    int v = idx / P;
-    int p = idx % P;
-    int X = p % w, Y = p / w;
+    const long long P = (long long)h * w;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= P) return;
+    const int p = (int)pix;
+    const int X = p % w, Y = p / w;
+    for (int v = 0; v < nv; ++v) {
+    const long long idx = v * P + p;
     const float *f = FM + (size_t)idx * 5;
     const float4 *L = img0 + (size_t)vt.cam_l[v] * P;
     const float4 *R = img0 + (size_t)vt.cam_r[v] * P;
@@ -192,6 +198,7 @@ __global__ void final_blend_kernel(const float4 *img0, const float *FM, const Vi
     o[1] = M * a.y + (1.f - M) * b.y;
     o[2] = M * a.z + (1.f - M) * b.z;
     store_px(u0 + (size_t)idx * cs, vals, cs);
+    }
 }
 
 // Bilinear sample of 8 consecutive channels (bf16 storage, 16-byte loads).
@@ -234,20 +241,21 @@ __device__ __forceinline__ void store8(bf16 *d, const float (&v)[8]) {
 // a6: flow pyramid level k: F_k = box2(F_{k-1}) / 2 (4 channels; F_0 = the final
 // flow with stride 5), then warp both cameras' context features of this level
 // by F_k[0:2] / F_k[2:4] into channel slots of the U-Net level tensor.
-// One thread per (view, pixel, group of 8 channels).
+// One thread per (pixel, group of 8 channels) walks the views (the context features
+// of a camera are gathered by every view that uses it).
 template <typename T>
 __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C,
                                 const ViewTab vt, int nv, int h, int w, int circ,
                                 T *dst, int dst_cs, int off_l, int off_r) {
-    int groups = C / 8;
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long P = (long long)h * w;
-    if (idx >= (long long)nv * P * groups) return;
-    int g = idx % groups;
-    long long vp = idx / groups;
-    int v = vp / P;
-    int p = vp % P;
-    int X = p % w, Y = p / w;
+    const int groups = C / 8;
+    const long long P = (long long)h * w;
+    const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= P * groups) return;
+    const int g = (int)(gi % groups);
+    const int p = (int)(gi / groups);
+    const int X = p % w, Y = p / w;
+    for (int v = 0; v < nv; ++v) {
+    const long long vp = v * P + p;
     const float *fp = Fprev + (size_t)v * (P * 4) * fprev_cs;
     int W2 = 2 * w;
     float F[4];
@@ -271,6 +279,7 @@ __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, con
     store8(d + off_l + g * 8, o);
     bilerp8(cr, C, g * 8, tr, o);
     store8(d + off_r + g * 8, o);
+    }
 }
 
 // a8: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to H x W.
@@ -320,7 +329,7 @@ int launch_vib0_input(const float4 *img2, const ViewTab &vt, int nv, int h, int 
 template <typename T>
 int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *x, int cs, cudaStream_t st) {
-    long long n = (long long)nv * h * w;
+    long long n = (long long)h * w;
     stage_input_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, circ, x, cs);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
@@ -336,7 +345,7 @@ int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ
 template <typename T>
 int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *u0, int cs, float *ib, cudaStream_t st) {
-    long long n = (long long)nv * h * w;
+    long long n = (long long)h * w;
     final_blend_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(img0, FM, vt, nv, h, w, circ, u0, cs, ib);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
@@ -345,7 +354,7 @@ int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, i
 template <typename T>
 int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, const ViewTab &vt,
                     int nv, int h, int w, int circ, T *dst, int dst_cs, int off_l, int off_r, cudaStream_t st) {
-    long long n = (long long)nv * h * w * (C / 8);
+    long long n = (long long)h * w * (C / 8);
     ctx_warp_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(Fprev, fprev_cs, Fk, ctx, C, vt, nv, h, w, circ,
                                                            dst, dst_cs, off_l, off_r);
     FVV_LAUNCH_CHECK();
