@@ -176,13 +176,15 @@ __global__ void residual_kernel(const float *FMp, float *res, int nv, int h, int
 // Writes the refinement input [I_l->m, I_r->m] (zero-padded to cs) and I_blend.
 // One thread per pixel walks the views (image taps shared across views stay in cache).
 template <typename T>
-__global__ void final_blend_kernel(const float4 *img0, const float *FM, const ViewTab vt, int nv,
-                                   int h, int w, int circ, T *u0, int cs, float *ib) {
+__global__ void final_blend_kernel(const float4 *__restrict__ img0, const float *__restrict__ FM, const ViewTab vt,
+                                   int nv, int h, int w, int circ, T *__restrict__ u0, int cs, float *__restrict__ ib) {
     const long long P = (long long)h * w;
     const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= P) return;
     const int p = (int)pix;
     const int X = p % w, Y = p / w;
+    // two views in flight per thread (their gathers overlap)
+#pragma unroll 2
     for (int v = 0; v < nv; ++v) {
     const long long idx = v * P + p;
     const float *f = FM + (size_t)idx * 5;
