@@ -36,7 +36,7 @@ FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 
 # DRAM bytes (read + write) of one vib2.m launch at this workload, from one ncu capture
 # each (profiles/conv_tc_halo_pair_vib2_m1_1080p_7views.md and
 # profiles/conv_tc_fp8_halo_pair_vib2_m1_1080p_7views.md); refresh when the kernel changes
-TRAFFIC_VIB2_M = {"bf16": 469_191_168 + 430_624_512, "fp8": 234_666_496 + 196_963_072}
+TRAFFIC_VIB2_M = {"bf16": 469_221_376 + 431_349_504, "fp8": 234_637_824 + 197_475_072}
 
 
 def peaks():
