@@ -151,9 +151,6 @@ template <int BN, int MT> struct AccCfg {
 // on a clamped tile and not stored).
 // GRP = 1 (halo, small N): one stage holds a (row tap, channel block)'s A box AND its
 // three weight slices, so the MMA thread syncs once per 3 x (row bytes / 32) MMAs.
-// HT = 1 (halo, 4-phase transposed conv): the tile is MT rows x 128 pixels of one
-// phase's input grid; per channel block ONE box of (MT + 1) rows x 129 pixels feeds the
-// phase's four taps, whose operands start 0/1 rows and 0/1 pixels into it.
 // S2H = 1 (stride-2 3x3 conv whose input pixel is one channel block of 16 or 32 channels):
 // the tile is one row of 128 output pixels; per row tap ky ONE box of 129 pixel PAIRS
 // (the 5-D pair view, pair rows of 64 or 128 bytes) feeds the three column taps: kx = 1
@@ -162,25 +159,22 @@ template <int BN, int MT> struct AccCfg {
 // resident in shared memory (loaded once per CTA).  K order (ky, kx, k) as on the
 // per-tap path.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0, int GRP = 0, int HT = 0, int S2H = 0>
+          int MC = 0, int GRP = 0, int S2H = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = S2H ? 129 * 2 * ROW_BYTES
-                                     : (HT ? (MT + 1) * 129 * ROW_BYTES
-                                           : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES)),
+    constexpr uint32_t A_BYTES = S2H ? 129 * 2 * ROW_BYTES : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES),
                        B_BYTES = BN * ROW_BYTES;
-    constexpr int HROW = HT ? 129 : 130;  // pixels per row of a halo box
-    constexpr int NB = HT ? 4 : 3;        // weight slices per halo box
+    constexpr int HROW = 130; // pixels per row of a halo box
+    constexpr int NB = 3;     // weight slices (column taps) per halo box
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
     static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
     // (BN % 8 == 0: each weight slice of a grouped box starts on a swizzle-pattern boundary)
     static_assert(!GRP || (HALO && !MC && BN % 8 == 0), "grouped stages run on the halo path");
-    static_assert(!HT || (HALO && !MC && !GRP), "transposed-conv halo runs on the split-ring path");
-    static_assert(!S2H || (!HALO && !MC && !GRP && !HT && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
+    static_assert(!S2H || (!HALO && !MC && !GRP && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
                            (ROW_BYTES == 32 || ROW_BYTES == 64)),
                   "stride-2 pair halo: one 16/32-channel block, pair rows of 64/128 bytes");
     constexpr uint32_t BR_STRIDE = (9 * B_BYTES + 1023) & ~1023u; // S2H: the resident weight slices
@@ -314,19 +308,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int t = blockIdx.x; t < t_end && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
                 tile_coords(p, t < p.num_tiles ? t : p.num_tiles - 1, ph, n, y0, x0);
-                // boxes in K order: (ky, channel block) for 3x3 taps, channel block for the phase's taps
-                const int ngroups = HT ? p.nck : 3 * p.nck;
+                // boxes in K order (ky, channel block)
+                const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && !stop; ++grp) {
-                        const int ky = HT ? 0 : grp / p.nck, c = HT ? grp : grp - ky * p.nck;
+                        const int ky = grp / p.nck, c = grp - ky * p.nck;
                         if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
                         uint32_t fa = ptx::smem_u32(&bars->full[sa]);
                         ptx::mbar_arrive_expect_tx(fa, A_BYTES);
-                        if (HT) // rows y0 + dy_min .., pixels x0 + dx_min .. (dy, dx in {-1, 0} or {0, 1} by phase)
-                            ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK,
-                                             x0 - ((ph & 1) ? 0 : 1), y0 - ((ph >> 1) ? 0 : 1), n);
-                        else
-                            ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
-                                             y0 + ky - 1, n);
+                        ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
+                                         y0 + ky - 1, n);
                         ++issued_a;
                         if (++sa == STAGES) { sa = 0; pa ^= 1; }
                         for (int kx = 0; kx < NB; ++kx) {
@@ -338,8 +328,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 ptx::tma_load_3d_mc(ptx::smem_u32(sB + sb * B_STRIDE) + rank * (B_BYTES / 2), &tmB, fbb,
                                                     c * CK, (int)rank * (BN / 2), ky * 3 + kx, (uint16_t)3);
                             else
-                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0,
-                                                 HT ? ph * 4 + kx : ky * 3 + kx);
+                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
                             ++issued_b;
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
@@ -521,7 +510,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const uint32_t d = tmem + acc * (MT * BN);
                 bool ok = true;
                 uint32_t accumulate = 0;
-                const int ngroups = HT ? p.nck : 3 * p.nck;
+                const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && ok; ++grp) {
                         if (!wait_bar(ptx::smem_u32(&bars->full[sa]), pa, abort, p.err, 3)) { ok = false; break; }
                         ptx::tc_fence_after();
@@ -538,9 +527,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
 #pragma unroll
                                 for (int m = 0; m < MT; ++m) {
-                                    // 3x3: row block m, column tap kx; transposed: tap (ty, tx) =
-                                    // (kx >> 1, kx & 1) reads box row m + 1 - ty, pixel 1 - tx on
-                                    const int row0 = HT ? (m + 1 - (kx >> 1)) * HROW + 1 - (kx & 1) : m * HROW + kx;
+                                    const int row0 = m * HROW + kx; // row block m, column tap kx
                                     uint64_t ad = ptx::smem_desc(a0 + row0 * ROW_BYTES + k * 32, ROW_BYTES);
                                     if (F8) ptx::mma_f8(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
                                     else ptx::mma_bf16(d + m * BN, ad, bd, IDESC, accumulate | (uint32_t)k);
@@ -698,10 +685,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // Each warp writes its 32 rows chunk by chunk (STG_ROW bytes of channels per
             // row) into a swizzled staging buffer and one lane stores the box with TMA
             // (rows outside the output are clipped by the tensor map).  bf16 or E4M3.
+            // A chunk is min(BN, 64) (bf16) or min(BN, 128) (E4M3) columns; for the 4-phase
+            // transposed conv (MODE_T3) it is one phase's C_out columns, stored through
+            // the pixel-pair map at that phase's row and column parity.
             const int oes = p.out_fp8 ? 1 : 2;
-            const int chb = BN * oes < 128 ? BN * oes : 128, chn = chb / oes;
-            // chn = min(BN, 64) (bf16) or min(BN, 128) (E4M3) columns per chunk: a multiple of 16 * LDB
-            constexpr int LDB = BN >= 64 ? (CTAS <= 2 ? 4 : 2) : (BN == 32 ? 2 : 1);
+            // (staged stores of the 4-phase convT exist for N = 128 only; other tiles compile without them)
+            const bool t3 = BN == 128 && p.mode == MODE_T3;
+            const int chn = t3 ? p.co : (BN * oes < 128 ? BN : 128 / oes), chb = chn * oes;
+            const int ncol = t3 ? 4 * p.co : BN;
+            constexpr int LDB = BN >= 64 ? (CTAS <= 2 ? 4 : 2) : (BN == 32 ? 2 : 1); // divides chn / 16
             const uint32_t swm = chb == 128 ? 7u : (chb == 64 ? 3u : 1u);
 #pragma unroll 1
             for (int m = 0; m < MT; ++m) {
@@ -711,30 +703,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const int by = y0 + (rb >> p.tw_log), bx = x0 + (rb & (tw - 1));
                 const uint32_t tb = tbase + m * BN;
 #pragma unroll 1
-                for (int k0 = 0; k0 < BN; k0 += chn) {
+                for (int k0 = 0; k0 < ncol; k0 += chn) {
                     // the buffer staged two chunks ago must have been read by its store
                     // the buffer's previous store (NSB chunks ago) must have been read
                     if (lane == 0) ptx::bulk_wait_read<NSB - 1>();
                     __syncwarp();
                     const uint32_t sbuf = stg_warp + (scnt % NSB) * STG_BYTES;
-#pragma unroll 1
-                    for (int cb = k0; cb < k0 + chn; cb += 16 * LDB) {
-                        // LDB accumulator loads in flight per wait (their latency overlaps)
-                        uint32_t rr[LDB][16];
-                        __syncwarp();
-#pragma unroll
-                        for (int u = 0; u < LDB; ++u) ptx::tmem_ld16(tb + cb + 16 * u, rr[u]);
-                        ptx::tmem_ld_wait();
-#pragma unroll
-                        for (int u = 0; u < LDB; ++u) {
-                        const int c = cb + 16 * u;
-                        const uint32_t(&r)[16] = rr[u];
+                    // bias, ReLU, conversion and swizzled staging of columns c .. c + 15
+                    // (output channels cc .. cc + 15)
+                    auto stage16 = [&](int c, int cc, const uint32_t(&r)[16]) {
                         float v[16];
                         float vmax = 0.f;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            float sc = p.acc_scale ? __ldg(p.acc_scale + c + j) : 1.f;
-                            float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + c + j);
+                            float sc = p.acc_scale ? __ldg(p.acc_scale + cc + j) : 1.f;
+                            float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + cc + j);
                             v[j] = p.relu ? fmaxf(a, 0.f) : a;
                             vmax = fmaxf(vmax, fabsf(v[j]));
                         }
@@ -758,6 +741,30 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), w0);
                             ptx::st_shared_v4(a1 ^ (((a1 >> 7) & swm) << 4), w1);
                         }
+                    };
+                    if (t3) {
+                        // one phase: C_out (a multiple of 32) columns, two loads per wait
+#pragma unroll 1
+                        for (int cb = k0; cb < k0 + chn; cb += 32) {
+                            uint32_t r0[16], r1[16];
+                            __syncwarp();
+                            ptx::tmem_ld16(tb + cb, r0);
+                            ptx::tmem_ld16(tb + cb + 16, r1);
+                            ptx::tmem_ld_wait();
+                            stage16(cb, cb - k0, r0);
+                            stage16(cb + 16, cb + 16 - k0, r1);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int cb = k0; cb < k0 + chn; cb += 16 * LDB) {
+                            // LDB accumulator loads in flight per wait (their latency overlaps)
+                            uint32_t rr[LDB][16];
+                            __syncwarp();
+#pragma unroll
+                            for (int u = 0; u < LDB; ++u) ptx::tmem_ld16(tb + cb + 16 * u, rr[u]);
+                            ptx::tmem_ld_wait();
+#pragma unroll
+                            for (int u = 0; u < LDB; ++u) stage16(cb + 16 * u, cb + 16 * u, rr[u]);
                         }
                     }
                     ptx::fence_proxy_async_smem();
@@ -765,6 +772,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     if (lane == 0 && !phantom) {
                         if (p.mode == MODE_T)
                             ptx::tma_store_5d(&tmC, sbuf, (ph & 1) * p.out_cs + p.out_coff + k0, bx, ph >> 1, by, n);
+                        else if (t3) // phase k0 / C_out: output row parity >> 1, column parity & 1
+                            ptx::tma_store_5d(&tmC, sbuf, ((k0 / p.co) & 1) * p.out_cs + p.out_coff, bx,
+                                              (k0 / p.co) >> 1, by, n);
                         else
                             ptx::tma_store_4d(&tmC, sbuf, p.out_coff + k0, bx, by, n);
                         ptx::bulk_commit();
@@ -1126,7 +1136,7 @@ template <int BN, int CK, int TS>
 int launch_s2h(const CUtensorMap &ma, const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p,
                cudaStream_t st) {
     using C = S2hCfg<BN, CK, TS>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 0, C::STAGES, TS, 0, 0, 0, 1>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 0, C::STAGES, TS, 0, 0, 1>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1158,54 +1168,6 @@ int dispatch_s2h_ts(int bn, int ck, const CUtensorMap &ma, const CUtensorMap &mb
     if (bn == 32 && ck == 16) return launch_s2h<32, 16, TS>(ma, mb3, mc, p, st);
     if (bn == 64 && ck == 32) return launch_s2h<64, 32, TS>(ma, mb3, mc, p, st);
     set_error("no stride-2 halo kernel for N=%d, CK=%d", bn, ck);
-    return FVV_EINVAL;
-}
-
-// Transposed-conv halo (4-phase convT, 128-byte rows): a box of (MT + 1) x 129 pixels
-// per channel block, two A stages, the weight ring takes the rest of the budget.
-template <int BN, int TS, int MT> struct HaloTCfg {
-    static constexpr uint32_t A = ((MT + 1) * 129 * 128 + 1023) & ~1023u, B = ((BN * 128) + 1023) & ~1023u;
-    static constexpr uint32_t STG = stg_bytes(BN, TS, MT);
-    static constexpr int CTAS = BN <= 32 ? 2 : 1, STAGES = 2;
-    static constexpr int fit = (int)((kSmemBudget / CTAS - 2048 - STG - STAGES * A) / B);
-    static constexpr int STAGES_B = fit > 12 ? 12 : fit;
-    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
-    static_assert(STAGES_B >= 4 && CTAS * AccCfg<BN, MT>::TMEM_COLS <= 512, "transposed halo config");
-};
-
-template <int BN, int TS, int MT>
-int launch_halo_t(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
-                  cudaStream_t st) {
-    using C = HaloTCfg<BN, TS, MT>;
-    auto kern = conv_tc_kernel<BN, 64, MT, C::STAGES, C::CTAS, 0, 1, C::STAGES_B, TS, 0, 0, 1>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-        attr_set = true;
-    }
-    if (!g_num_sms) {
-        int dev;
-        FVV_CHECK_CUDA(cudaGetDevice(&dev));
-        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    int slots = g_num_sms * C::CTAS;
-    int grid = p.num_tiles < slots ? p.num_tiles : slots;
-    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
-    count_launch();
-    FVV_CHECK_CUDA(cudaGetLastError());
-    return FVV_OK;
-}
-
-// Measured on the 1080p forward: 15% faster for N = 32 (RefineNet d2); slower for
-// N = 64 (d1, one CTA per SM) and N = 128 with two row blocks (VIB t0), which keep
-// the per-tap boxes.
-bool halo_t_ok(int bn, int ck, int es, bool f8) { return !f8 && ck * es == 128 && bn == 32; }
-
-template <int TS>
-int dispatch_halo_t_ts(int bn, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
-                       cudaStream_t st) {
-    if (bn == 32) return launch_halo_t<32, TS, 1>(ma, mb, mc, p, st);
-    set_error("no transposed-conv halo kernel for N=%d", bn);
     return FVV_EINVAL;
 }
 
@@ -1356,7 +1318,9 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
     return FVV_OK;
 }
 
-bool tc_all_phases(int li) { return kLayers[li].kind == K_CONVT && 4 * kLayers[li].co <= 64; }
+// (C_out <= 32: VIB t1, RefineNet d2 and d3; one A fetch per MMA then serves the four
+// phases' columns, which outweighs the zero taps for these narrow layers)
+bool tc_all_phases(int li) { return kLayers[li].kind == K_CONVT && 4 * kLayers[li].co <= 128; }
 
 int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win, void *out,
             int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi) {
@@ -1385,19 +1349,15 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         int tw = force < pix_log ? force : pix_log;
         if (pix_log - tw <= 8) s = Shape{pix_log - tw, tw};
     }
-    // default tile of the 3x3 stride-1 layers with 128-byte operand rows: one row of
-    // 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
-    // the 4-phase transposed convs: one (MT + 1)-row box per channel block feeds the
-    // phase's four taps (MT = the layer's row blocks: 2 for N = 128)
-    const bool halo_t = force < 0 && p.mode == MODE_T && halo_t_ok(bn, ck, es, f8) && p.gw >= 96 &&
-                        (!epi || epi->mode == EPI_STORE);
-    const bool halo = halo_t || (force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
-                                 p.gw >= 96);
+    // default tile of the 3x3 stride-1 layers (and the all-phase transposed convs): one
+    // row of 128 pixels, A loaded once per (ky, channel block) as a 130-pixel halo box
+    const bool halo = force < 0 && (p.mode == MODE_S1 || p.mode == MODE_T3) && halo_ok(bn, ck, es, f8) &&
+                      p.gw >= 96;
     // stride-2 layers whose input pixel is exactly one 16/32-channel block: one row of 128
     // output pixels, one box of 129 pixel pairs per row tap, resident weights
     const bool s2h = force < 0 && p.mode == MODE_S2 && !f8 && cip == ck && in_cs == cip && in_coff == 0 &&
                      s2h_ok(bn, ck) && p.gw >= 96 && (!epi || epi->mode == EPI_STORE);
-    const int halo_mt = halo_t ? mt : (bn == 256 ? kHaloMT256 : 1);
+    const int halo_mt = bn == 256 ? kHaloMT256 : 1;
     if (halo) s = Shape{halo_mt - 1, 7};
     if (s2h) s = Shape{0, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
@@ -1447,9 +1407,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        // halo boxes: MT rows x 130 pixels (3x3), (MT + 1) rows x 129 pixels (4-phase convT)
-        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo_t ? tw_ + 1 : (halo ? tw_ + 2 : tw_)),
-                             (cuuint32_t)(halo_t ? th_ + 1 : th_), 1};
+        // halo boxes: MT rows x 130 pixels
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1};
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
     g_encode_u8 = false;
@@ -1458,15 +1417,20 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     // (every output channel of the tile is a real channel: C_out = N tile)
     CUtensorMap mc = ma;
     {
-        const int oes = p.out_fp8 ? 1 : 2, chb = bn * oes < 128 ? bn * oes : 128;
-        p.tma_store = (!epi || epi->mode == EPI_STORE) && !out_f32 && p.mode != MODE_T3 && L.co == bn &&
+        // (MODE_T3: one chunk per phase, C_out columns wide; only for N = 128 (RefineNet
+        // d2): d3 (N = 64) keeps its grouped stages at two CTAs per SM, measured 2x faster
+        // than with the staging buffers)
+        const int oes = p.out_fp8 ? 1 : 2;
+        const int chb = p.mode == MODE_T3 ? L.co * oes : (bn * oes < 128 ? bn * oes : 128);
+        p.tma_store = (!epi || epi->mode == EPI_STORE) && !out_f32 &&
+                      (p.mode == MODE_T3 ? 4 * L.co == bn && bn == 128 && L.co % 32 == 0 : L.co == bn) &&
                       (chb == 32 || chb == 64 || chb == 128) && (out_cs * oes) % 16 == 0 &&
                       (out_coff * oes) % 16 == 0 && ((uintptr_t)out % 16) == 0;
         if (p.tma_store) {
             const cuuint64_t oe = (cuuint64_t)oes;
             const cuuint32_t bw = tw_ < 32 ? tw_ : 32, bh = 32 / bw;
             g_encode_u8 = p.out_fp8 != 0;
-            if (p.mode == MODE_T) {
+            if (p.mode == MODE_T || p.mode == MODE_T3) {
                 cuuint64_t dims[5] = {(cuuint64_t)2 * out_cs, (cuuint64_t)p.gw, 2, (cuuint64_t)p.gh, (cuuint64_t)N};
                 cuuint64_t strides[4] = {(cuuint64_t)2 * out_cs * oe, (cuuint64_t)p.out_w * out_cs * oe,
                                          (cuuint64_t)2 * p.out_w * out_cs * oe,
@@ -1487,9 +1451,6 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     if (s2h)
         return p.tma_store ? dispatch_s2h_ts<1>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st)
                            : dispatch_s2h_ts<0>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st);
-    if (halo_t)
-        return p.tma_store ? dispatch_halo_t_ts<1>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st)
-                           : dispatch_halo_t_ts<0>(bn, ma, *(const CUtensorMap *)tw.map, mc, p, st);
     if (halo)
         return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half,
                              *(const CUtensorMap *)tw.map3, mc, p, st);

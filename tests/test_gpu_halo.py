@@ -15,7 +15,11 @@ column taps read it 0, 1, 2 rows in.  Checks:
 * the whole BF16 forward with the halo tiles equals, bit for bit, the same
   forward with every layer forced onto plain 1 x 128 tiles: both accumulate
   the K loop in the order (row tap, channel block, column tap), or (channel block,
-  tap) for the 4-phase transposed convs.
+  tap) for the per-phase transposed convs.
+
+The transposed convs with C_out <= 32 (VIB t1, RefineNet d2, d3) run as one 3x3 conv
+over all four output phases (N = 4 C_out); d2's phases are stored by TMA through the
+pixel-pair map, one phase per staged chunk.
 """
 import json
 
@@ -30,7 +34,7 @@ from tests.gpu_common import blob, pair
 pytestmark = pytest.mark.gpu
 
 # 128-byte rows (C_in >= 64), the narrow 32- / 64-byte rows (C_in = 16, 32) and the
-# 4-phase transposed convs (one (row blocks + 1) x 129-pixel box per channel block)
+# all-phase transposed convs (t1, d3, and d2 with TMA-stored phases)
 HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3", "ctx.c1", "ctx.c3",
                "ref.e0b", "ref.d2"]
 
@@ -85,6 +89,35 @@ def test_halo_layer_matches_oracle(torch_cuda, name):
         scale = max(1.0, float(np.abs(ref).max()))
         err = np.abs(got[i, ..., 2:2 + co] - ref).max()
         assert err <= 1e-4 * scale, (name, i, err, scale)
+
+
+@pytest.mark.parametrize("name", ["ref.d2", "vib2.t0"])
+def test_transposed_conv_tma_store_bf16(torch_cuda, name):
+    """BF16 outputs of the transposed convs written through the pixel-pair TMA-store map:
+    RefineNet d2 (all four phases in one tile, one staged chunk per phase) and VIB t0
+    (one phase per tile), into a channel slot of a wider tensor."""
+    torch = torch_cuda
+    names = [m[0] for m in weights.manifest()]
+    li = names.index(name)
+    _, kind, ci, co, _, relu = weights.manifest()[li]
+    rng = np.random.default_rng(700 + li)
+    H, W, n = 3, 131, 2
+    x = _bf16_round(torch, rng.standard_normal((n, H, W, ci)) * 0.5)
+    wv, bv = weights.layer_views(blob())[name]
+    wq = _bf16_round(torch, wv)
+    it = fvv.Interpolator(blob(), 64, 64, precision=fvv.FVV_BF16, max_views=1)
+    ocs, ooff = co + 32, 16
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    out = torch.full((n, 2 * H, 2 * W, ocs), -7.0, dtype=torch.bfloat16, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, ci, 0, n, H, W, out, ocs, ooff, False)
+    fvv.fvv_interp_status(it.h)
+    got = out.float().cpu().numpy()
+    assert (got[..., :ooff] == -7).all() and (got[..., ooff + co:] == -7).all(), "wrote outside its channel slot"
+    for i in range(n):
+        ref = oracle.conv_transpose4x4(x[i], wq, bv, relu=relu)
+        scale = max(1.0, float(np.abs(ref).max()))
+        err = np.abs(got[i, ..., ooff:ooff + co] - ref) - np.abs(ref) * 2.0 ** -8
+        assert err.max() <= 1e-4 * scale, (name, i, float(err.max()), scale)
 
 
 # stride-2 convs whose input pixel is one 16- or 32-channel block: one box of 129 pixel
