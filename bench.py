@@ -33,10 +33,13 @@ TS = [k / 8 for k in range(1, 8)]
 METRIC = "1080p virtual views/s"
 SCENE_SEED, WEIGHT_SEED, MAX_DISP = 2, 0, 64.0
 FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
-# DRAM bytes (read + write) of one vib2.m launch at this workload, from one ncu capture
-# each (profiles/conv_tc_halo_pair_vib2_m1_1080p_7views.md and
-# profiles/conv_tc_fp8_halo_pair_vib2_m1_1080p_7views.md); refresh when the kernel changes
+# DRAM bytes (read + write) of one vib2.m launch at 7 views, from one ncu capture each
+# (profiles/conv_tc_halo_pair_vib2_m1_1080p_7views.md and
+# profiles/conv_tc_fp8_halo_pair_vib2_m1_1080p_7views.md); a launch's traffic is its
+# views' activations, so other view counts scale it by views / 7.  Refresh when the
+# kernel changes.
 TRAFFIC_VIB2_M = {"bf16": 469_221_376 + 431_349_504, "fp8": 234_637_824 + 197_475_072}
+TRAFFIC_VIEWS = 7
 
 
 def peaks():
@@ -484,7 +487,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=3)
-    ap.add_argument("--views", type=int, default=7, help="views per step (t = k/(views+1))")
+    ap.add_argument("--views", type=int, default=None,
+                    help="views per step (t = k/(views+1)); default 7 (15 with --precision fp8)")
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed steps (for profiling)")
     ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve", "serve-dense", "stitch"],
                     help="pair: the headline 1-pair 7-view step; rig: batched 9-camera instants; "
@@ -492,6 +496,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     global TS
+    if args.views is None:   # the 1080p pair workloads: 7 views at t = k/8, FP8: 15 at t = k/16
+        args.views = 15 if args.precision == "fp8" else 7
     TS = [k / (args.views + 1) for k in range(1, args.views + 1)]
     args.warmup = max(args.warmup, 3)
 
@@ -613,13 +619,13 @@ def main():
         roof = {"bound": "tensor", "kernel": "conv_tc_kernel E4M3 halo, cluster pairs (tcgen05 kind::f8f6f4): vib2.m0-m5",
                 "achieved": m_fl / (m_ms / 1e3) / 1e12, "peak": 2 * pk["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained x 2 (fp8/bf16 nominal ratio)",
-                "traffic": TRAFFIC_VIB2_M.get("fp8"), "launch_us": m_ms / max(m_n, 1) * 1e3,
+                "traffic": round(TRAFFIC_VIB2_M["fp8"] * len(TS) / TRAFFIC_VIEWS), "launch_us": m_ms / max(m_n, 1) * 1e3,
                 "all_convs_tflops": conv_fl / (conv_ms / 1e3) / 1e12}
     else:
         roof = {"bound": "tensor", "kernel": "conv_tc_kernel BF16 halo, cluster pairs (tcgen05 kind::f16): vib2.m0-m5",
                 "achieved": m_fl / (m_ms / 1e3) / 1e12, "peak": pk["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained",
-                "traffic": TRAFFIC_VIB2_M.get("bf16"), "launch_us": m_ms / max(m_n, 1) * 1e3,
+                "traffic": round(TRAFFIC_VIB2_M["bf16"] * len(TS) / TRAFFIC_VIEWS), "launch_us": m_ms / max(m_n, 1) * 1e3,
                 "all_convs_tflops": conv_fl / (conv_ms / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     if args.precision != "fp32":
@@ -662,6 +668,10 @@ def main():
                 "fp32_vs_fp64": {"max_abs_err": float(np.abs(out32[mid] - ref).max()),
                                  "psnr_db": psnr(out32[mid], ref)},
                 "view": "t=0.5"}
+            if args.precision != "fp32":
+                line["parity"][f"{args.precision}_vs_fp32"] = {
+                    "max_abs_err": float(np.abs(out_main[mid] - out32[mid]).max()),
+                    "psnr_db": psnr(out_main[mid], out32[mid])}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
