@@ -197,8 +197,9 @@ int fvv_stitch_cluster(const float *center, const float *const *side_views, int 
 int fvv_interp_status(fvv_interp *h);
 
 /* FP8 calibration (FVV_FP8 handles only; required before their first run).
- * On FP8 handles the six 256 -> 256 convs of every VIBlock (72% of the FLOPs,
- * Table 3) run with E4M3 operands and FP32 accumulation: weights carry one scale
+ * On FP8 handles every VIBlock conv with 128 or 256 input channels -- c1, the six
+ * 256 -> 256 convs and the transposed t0 (89% of the FLOPs, Table 3) -- runs with
+ * E4M3 operands and FP32 accumulation: weights carry one scale
  * per output channel, s_w = max |w| / 448, fixed at create; each such conv's input
  * carries one scale per tensor, s_a = (max |input| over the calibration views) /
  * 448, measured here by running the network in BF16 on n_pairs frame pairs at

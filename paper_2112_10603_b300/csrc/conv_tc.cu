@@ -931,7 +931,7 @@ Shape pick_shape(int gh, int gw, int pix_log) {
 // Row blocks per tile: two for the wide layers (the weight slice then feeds two MMAs).
 // (N = 256 keeps one block: two 256-column accumulators would fill TMEM and lose the
 // double buffering that hides the epilogue.)
-int mt_for(int bn, int ck) { return ck == 64 && bn == 128 ? 2 : 1; }
+int mt_for(int bn, int ck, int es) { return ck * es == 128 && bn == 128 ? 2 : 1; }
 
 // Resources of one (N tile, channel block, row blocks) configuration.  Small-N
 // configs put several CTAs on an SM (their TMEM columns and shared memory allow
@@ -960,7 +960,7 @@ int g_num_sms = 0;
 template <int BN, int CK, int F8, int TS>
 int launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                cudaStream_t st) {
-    constexpr int MT = (!F8 && CK == 64 && BN == 128) ? 2 : 1; // = mt_for(BN, CK)
+    constexpr int MT = (CK * (F8 ? 1 : 2) == 128 && BN == 128) ? 2 : 1; // = mt_for(BN, CK, ES)
     using C = Cfg<BN, CK, MT, F8, TS>;
     auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8, 0, C::STAGES, TS>;
     static bool attr_set = false;
@@ -1176,6 +1176,7 @@ int dispatch_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMa
                 const TcParams &p, cudaStream_t st) {
     if (f8) {
         if (bn == 256 && ck == 128) return launch_cfg<256, 128, 1, TS>(ma, mb, mc, p, st);
+        if (bn == 128 && ck == 128) return launch_cfg<128, 128, 1, TS>(ma, mb, mc, p, st);
         set_error("no FP8 tensor-core kernel for N=%d, CK=%d", bn, ck);
         return FVV_EINVAL;
     }
@@ -1276,7 +1277,8 @@ int tc_prepare(fvv_interp *h, const float *blob) {
 }
 
 // E4M3 weights of the FP8 layers: per output channel s_w = max |w| / 448 over
-// its taps and input channels, codes = RNE-satfinite(w / s_w), layout [9][C_out][C_in].
+// its taps and input channels, codes = RNE-satfinite(w / s_w), layout [slice][C_out][C_in]
+// (9 conv taps, or the transposed conv's 16 phase x tap slices in the BF16 order).
 int tc_prepare_fp8(fvv_interp *h, const float *blob) {
     size_t off = 0;
     for (int i = 0; i < kNumLayers; ++i) {
@@ -1284,18 +1286,31 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         const float *w = blob + off;
         off += (size_t)L.ci * L.co * (L.kind == K_CONV ? 9 : 16) + L.co;
         if (!fp8_layer(i)) continue;
+        const bool conv = L.kind == K_CONV;
+        const int taps = conv ? 9 : 16; // conv taps, or phase x tap of the transposed conv
+        // kernel value of (output channel, input channel, kernel position): conv
+        // weights are [C_out][C_in][3][3], transposed-conv weights [C_in][C_out][4][4]
+        auto wv = [&](int co, int ci, int k) {
+            return conv ? w[((size_t)co * L.ci + ci) * 9 + k] : w[((size_t)ci * L.co + co) * 16 + k];
+        };
         std::vector<float> sw(L.co);
-        std::vector<uint8_t> pk((size_t)9 * L.co * L.ci);
+        std::vector<uint8_t> pk((size_t)taps * L.co * L.ci);
         for (int co = 0; co < L.co; ++co) {
             float m = 0.f;
-            for (int k = 0; k < L.ci * 9; ++k) m = fmaxf(m, fabsf(w[(size_t)co * L.ci * 9 + k]));
+            for (int ci = 0; ci < L.ci; ++ci)
+                for (int k = 0; k < (conv ? 9 : 16); ++k) m = fmaxf(m, fabsf(wv(co, ci, k)));
             sw[co] = m > 0.f ? m / 448.f : 1.f;
         }
-        for (int tap = 0; tap < 9; ++tap)
+        for (int g = 0; g < taps; ++g) {
+            // transposed conv slice g = phase (py, px) x tap (ty, tx): kernel row
+            // 1 + 2 ty (py = 0) or 2 ty (py = 1), the same for columns
+            const int py = g >> 3, px = (g >> 2) & 1, ty = (g >> 1) & 1, tx = g & 1;
+            const int k = conv ? g : (py == 0 ? 1 + 2 * ty : 2 * ty) * 4 + (px == 0 ? 1 + 2 * tx : 2 * tx);
             for (int co = 0; co < L.co; ++co)
                 for (int ci = 0; ci < L.ci; ++ci)
-                    pk[((size_t)tap * L.co + co) * L.ci + ci] = (uint8_t)__nv_cvt_float_to_fp8(
-                        w[((size_t)co * L.ci + ci) * 9 + tap] / sw[co], __NV_SATFINITE, __NV_E4M3);
+                    pk[((size_t)g * L.co + co) * L.ci + ci] =
+                        (uint8_t)__nv_cvt_float_to_fp8(wv(co, ci, k) / sw[co], __NV_SATFINITE, __NV_E4M3);
+        }
         TcWeights &tw = h->tc8[i];
         tw.ci_pad = L.ci;
         tw.co_pad = L.co;
@@ -1303,7 +1318,7 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         FVV_CHECK_CUDA(cudaMemcpy(tw.w, pk.data(), pk.size(), cudaMemcpyHostToDevice));
         FVV_TRY(dalloc(h, (void **)&h->q_acc[i], L.co * sizeof(float)));
         h->s_w[i] = sw;
-        cuuint64_t dims[3] = {(cuuint64_t)L.ci, (cuuint64_t)L.co, 9};
+        cuuint64_t dims[3] = {(cuuint64_t)L.ci, (cuuint64_t)L.co, (cuuint64_t)taps};
         cuuint64_t strides[2] = {(cuuint64_t)L.ci, (cuuint64_t)L.ci * L.co};
         cuuint32_t box[3] = {128, (cuuint32_t)L.co, 1};
         g_encode_u8 = true;
@@ -1342,7 +1357,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     else { p.gh = Hin; p.gw = Win; }
     p.out_h = L.kind == K_CONV ? p.gh : 2 * Hin;
     p.out_w = L.kind == K_CONV ? p.gw : 2 * Win;
-    const int mt = mt_for(bn, ck), pix_log = mt == 2 ? 8 : 7;
+    const int mt = mt_for(bn, ck, es), pix_log = mt == 2 ? 8 : 7;
     Shape s = pick_shape(p.gh, p.gw, pix_log);
     const int force = h->tile_force >= 0 ? h->tile_force : h->tile_tw[li]; // autotuned width
     if (force >= 0) {

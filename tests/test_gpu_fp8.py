@@ -1,5 +1,6 @@
-"""FP8 (E4M3) path: the six 256-channel convs of every VIBlock with per-output-channel
-weight scales and calibrated per-tensor activation scales, FP32 accumulation.
+"""FP8 (E4M3) path: every VIBlock conv with 128 or 256 input channels (c1, the six
+256-channel convs m0-m5, the transposed t0) with per-output-channel weight scales and
+calibrated per-tensor activation scales, FP32 accumulation.
 
 Kernel level: an FP8 layer on E4M3 input codes equals the oracle's conv of the
 dequantised operands (codes x scales): a product of two E4M3 values is exact in
@@ -75,6 +76,42 @@ def test_fp8_layer_matches_dequantised_oracle(torch_cuda, name, h, ww):
         ref = oracle.conv3x3(xq[i].astype(np.float64) * s_a, wq * s_w[:, None, None, None], b, relu=True)
         scale = max(1.0, float(np.abs(ref).max()))
         assert np.abs(got[i] - ref).max() <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("name", ["vib2.c1", "vib0.c1", "vib1.t0", "vib2.t0"])
+def test_fp8_strided_and_transposed_layers(torch_cuda, name):
+    """The stride-2 c1 (128 -> 256) and the transposed t0 (256 -> 128) on E4M3 codes
+    equal the oracle's conv of the dequantised operands, ragged tiles included."""
+    torch = torch_cuda
+    H, W = 64, 96
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=3)
+    fvv.fvv_calibrate_fp8(it.h, _calib_frames(torch, H, W), 2)
+    li = [m[0] for m in weights.manifest()].index(name)
+    _, kind, ci, co, stride, relu = weights.manifest()[li]
+    s_a, s_w = fvv.fvv_interp_fp8_scales(it.h, li, co)
+    assert s_a > 0 and (s_w > 0).all()
+    w, b = weights.layer_views(blob())[name]
+    # per output channel: conv weights are [C_out][C_in][3][3], transposed [C_in][C_out][4][4]
+    sw = s_w[:, None, None, None] if kind == "conv" else s_w[None, :, None, None]
+    wq_codes, wq = _e4m3(torch, w / sw)
+    rng = np.random.default_rng(li)
+    n, h, ww = 2, (6 if kind == "conv" else 3), (260 if kind == "conv" else 131)
+    x = np.maximum(rng.standard_normal((n, h, ww, ci)), 0) * (100 * s_a)
+    xq_codes, xq = _e4m3(torch, x / s_a)
+    xd = torch.from_numpy(np.ascontiguousarray(xq_codes)).cuda()
+    Ho, Wo = (h // 2, ww // 2) if kind == "conv" else (2 * h, 2 * ww)
+    out = torch.zeros((n, Ho, Wo, co), device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, ci, 0, n, h, ww, out, co, 0, True)
+    fvv.fvv_interp_status(it.h)
+    got = out.cpu().numpy()
+    for i in range(n):
+        xi = xq[i].astype(np.float64) * s_a
+        if kind == "conv":
+            ref = oracle.conv3x3(xi, wq * sw, b, stride=2, relu=relu)
+        else:
+            ref = oracle.conv_transpose4x4(xi, wq * sw, b, relu=relu)
+        scale = max(1.0, float(np.abs(ref).max()))
+        assert np.abs(got[i] - ref).max() <= 1e-4 * scale, (name, i)
 
 
 @pytest.mark.parametrize("H,W,seed,disp", [(256, 256, 1, 12.0)])
