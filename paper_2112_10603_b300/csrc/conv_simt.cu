@@ -27,6 +27,30 @@ __device__ __forceinline__ float load_in(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_in(const bf16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void store_out(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_out(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
+// 16 consecutive channels of one pixel: 16-byte stores where the address allows
+__device__ __forceinline__ void store16(float *p, const float (&v)[16]) {
+    if (((uintptr_t)p & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) reinterpret_cast<float4 *>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p[k] = v[k];
+    }
+}
+__device__ __forceinline__ void store16(bf16 *p, const float (&v)[16]) {
+    if (((uintptr_t)p & 15) == 0) {
+        __nv_bfloat162 h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        uint4 u[2];
+        memcpy(u, h, 32);
+        reinterpret_cast<uint4 *>(p)[0] = u[0];
+        reinterpret_cast<uint4 *>(p)[1] = u[1];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p[k] = __float2bfloat16_rn(v[k]);
+    }
+}
 
 __device__ __forceinline__ int wrap_or_mark(int i, int n, int circ) {
     if (circ) { i %= n; return i < 0 ? i + n : i; }
@@ -160,6 +184,8 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
     long long r = idx / a.Wo;
     int oy = r % a.Ho, n = r / a.Ho;
     const float *in = static_cast<const float *>(a.in);
+    // the frame pyramid's (R, G, B, 0) pixels: one 16-byte load per tap
+    const bool vin = a.in_cs == 4 && a.in_coff == 0 && ((uintptr_t)in & 15) == 0;
     float acc[16];
 #pragma unroll
     for (int co = 0; co < 16; ++co) acc[co] = 0.f;
@@ -169,19 +195,27 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
         int ix = wrap_or_mark(ox * a.stride + tap % 3 - 1, a.W, a.circ);
         if (iy < 0 || ix < 0) continue;
         const float *src = in + ((size_t)(n * a.H + iy) * a.W + ix) * a.in_cs + a.in_coff;
+        float v3[3];
+        if (vin) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
+            v3[0] = f.x; v3[1] = f.y; v3[2] = f.z;
+        } else {
 #pragma unroll
-        for (int ci = 0; ci < 3; ++ci) {
-            float v = __ldg(src + ci);
-#pragma unroll
-            for (int co = 0; co < 16; ++co) acc[co] = fmaf(v, ws[(tap * 3 + ci) * 16 + co], acc[co]);
+            for (int ci = 0; ci < 3; ++ci) v3[ci] = __ldg(src + ci);
         }
+#pragma unroll
+        for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+            for (int co = 0; co < 16; ++co) acc[co] = fmaf(v3[ci], ws[(tap * 3 + ci) * 16 + co], acc[co]);
     }
     Tout *dst = static_cast<Tout *>(a.out) + idx * a.out_cs + a.out_coff;
+    float o[16];
 #pragma unroll
     for (int co = 0; co < 16; ++co) {
         float v = acc[co] + bs[co];
-        store_out(dst + co, a.relu ? fmaxf(v, 0.f) : v);
+        o[co] = a.relu ? fmaxf(v, 0.f) : v;
     }
+    store16(dst, o);
 }
 
 // RefineNet's last layer (Conv2d 16 -> 3, then Sigmoid, Table 3) fused with the
