@@ -38,7 +38,7 @@ FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 
 # profiles/conv_tc_fp8_halo_pair_vib2_m1_1080p_7views.md); a launch's traffic is its
 # views' activations, so other view counts scale it by views / 7.  Refresh when the
 # kernel changes.
-TRAFFIC_VIB2_M = {"bf16": 469_221_376 + 431_349_504, "fp8": 234_637_824 + 197_475_072}
+TRAFFIC_VIB2_M = {"bf16": 469_220_864 + 431_511_808, "fp8": 234_667_008 + 197_800_448}
 TRAFFIC_VIEWS = 7
 
 
@@ -422,7 +422,9 @@ def run_stitch(args, rank, world, local):
     g = torch.Generator(device="cuda").manual_seed(11)
     views = [torch.rand((h, w, 3), device="cuda", generator=g) for _ in range(2 * n_side + 1)]
     out = torch.empty((3 * h, w, 3), device="cuda")
-    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    # L2 flushed by READING 256 MB between launches: a write flush would leave ~126 MB of
+    # dirty lines whose write-back lands inside this sub-millisecond kernel
+    flush = torch.zeros(256 * 2 ** 20 // 4, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream()
     for _ in range(3):
         fvv.fvv_stitch_cluster(views[0], views[1:], h, w, scale, out)
@@ -430,7 +432,7 @@ def run_stitch(args, rank, world, local):
     ts = []
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
+        flush.sum()
         a.record(s)
         fvv.fvv_stitch_cluster(views[0], views[1:], h, w, scale, out)
         b.record(s)
@@ -443,7 +445,8 @@ def run_stitch(args, rank, world, local):
     gbs = algo / (ms / 1e3) / 1e9
     line = {"metric": "cluster frames/s (1080p real view + 32 arc views downscaled x4)", "value": 1e3 / ms,
             "unit": "frames/s", "n_gpus": world, "higher_is_better": True, "dtype": "f32", "data": "random views",
-            "config": {"workload": "stitch: 1920x1080, n_side 16, scale 4 -> 1920x3240", "l2": "flushed"},
+            "config": {"workload": "stitch: 1920x1080, n_side 16, scale 4 -> 1920x3240",
+                       "l2": "flushed between launches (256 MB read outside the timed events)"},
             "ms": ms, "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                    "frac": gbs / pk["hbm_gbs"], "algorithmic_bytes": algo,
                                    "peak_source": f"{pk_kind} hbm_gbs"}}
