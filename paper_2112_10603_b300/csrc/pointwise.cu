@@ -121,6 +121,15 @@ __global__ void vib0_input_kernel(const float4 *img2, const ViewTab vt, int nv, 
     store_px(x + (size_t)idx * cs, vals, cs);
 }
 
+// Pixel of this thread in a grid of 32 x 8 tiles (blocks of 256 threads): the taps of a
+// tile's bilinear gathers overlap in rows as well as columns, so they share L1 lines.
+__device__ __forceinline__ bool tile_pixel(int h, int w, int &X, int &Y) {
+    const int tiles_x = (w + 31) / 32;
+    X = (int)(blockIdx.x % tiles_x) * 32 + (int)(threadIdx.x & 31);
+    Y = (int)(blockIdx.x / tiles_x) * 8 + (int)(threadIdx.x >> 5);
+    return X < w && Y < h;
+}
+
 // a3: stage s input [I_l, I_r, W_l, W_r, M_up, F_up(4), t] (18 ch, zero-padded to cs)
 // at the stage grid h x w, from the previous stage's flow/mask FMp (h/2 x w/2 x 5).
 // One thread per pixel walks the views: views of one camera pair gather the same
@@ -129,10 +138,9 @@ template <typename T>
 __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *x, int cs) {
     const long long P = (long long)h * w;
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= P) return;
-    const int p = (int)pix;
-    const int X = p % w, Y = p / w;
+    int X, Y;
+    if (!tile_pixel(h, w, X, Y)) return;
+    const int p = Y * w + X;
     for (int v = 0; v < nv; ++v) {
     const long long idx = v * P + p;
     const float *fm = FMp + (size_t)v * (P / 4) * 5;
@@ -179,10 +187,9 @@ template <typename T>
 __global__ void final_blend_kernel(const float4 *__restrict__ img0, const float *__restrict__ FM, const ViewTab vt,
                                    int nv, int h, int w, int circ, T *__restrict__ u0, int cs, float *__restrict__ ib) {
     const long long P = (long long)h * w;
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= P) return;
-    const int p = (int)pix;
-    const int X = p % w, Y = p / w;
+    int X, Y;
+    if (!tile_pixel(h, w, X, Y)) return;
+    const int p = Y * w + X;
     // two views in flight per thread (their gathers overlap)
 #pragma unroll 2
     for (int v = 0; v < nv; ++v) {
@@ -303,6 +310,8 @@ __global__ void output_kernel(const float *ib, const float *z, int z_cs, int nv,
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+// 256-thread blocks over 32 x 8 pixel tiles (a warp = 32 pixels of one row)
+inline unsigned tile_blocks(int h, int w) { return (unsigned)(((w + 31) / 32) * ((h + 7) / 8)); }
 
 } // namespace
 
@@ -331,8 +340,7 @@ int launch_vib0_input(const float4 *img2, const ViewTab &vt, int nv, int h, int 
 template <typename T>
 int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *x, int cs, cudaStream_t st) {
-    long long n = (long long)h * w;
-    stage_input_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, circ, x, cs);
+    stage_input_kernel<T><<<tile_blocks(h, w), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, circ, x, cs);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
@@ -347,8 +355,7 @@ int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ
 template <typename T>
 int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *u0, int cs, float *ib, cudaStream_t st) {
-    long long n = (long long)h * w;
-    final_blend_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(img0, FM, vt, nv, h, w, circ, u0, cs, ib);
+    final_blend_kernel<T><<<tile_blocks(h, w), 256, 0, st>>>(img0, FM, vt, nv, h, w, circ, u0, cs, ib);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
