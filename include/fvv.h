@@ -198,7 +198,7 @@ int fvv_interp_status(fvv_interp *h);
 
 /* FP8 calibration (FVV_FP8 handles only; required before their first run).
  * On FP8 handles every VIBlock conv with 128 or 256 input channels -- c1, the six
- * 256 -> 256 convs and the transposed t0 (89% of the FLOPs, Table 3) -- runs with
+ * 256 -> 256 convs and the transposed t0 and t1 (90% of the FLOPs, Table 3) -- runs with
  * E4M3 operands and FP32 accumulation: weights carry one scale
  * per output channel, s_w = max |w| / 448, fixed at create; each such conv's input
  * carries one scale per tensor, s_a = (max |input| over the calibration views) /

@@ -671,7 +671,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             const float ly = py ? 0.25f : 0.75f, lx = px ? 0.25f : 0.75f;
                             float up = (1.f - ly) * ((1.f - lx) * nb[py][px][co] + lx * nb[py][px + 1][co]) +
                                        ly * ((1.f - lx) * nb[py + 1][px][co] + lx * nb[py + 1][px + 1][co]);
-                            float x = __uint_as_float(r[j]) + __ldg(p.bias + co) + up * (co < 4 ? 2.f : 1.f);
+                            const float sc = p.acc_scale ? __ldg(p.acc_scale + co) : 1.f;
+                            float x = __uint_as_float(r[j]) * sc + __ldg(p.bias + co) + up * (co < 4 ? 2.f : 1.f);
                             size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
                             ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
                         }
@@ -1007,8 +1008,9 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
 // layers: the narrow 16/32-channel convs, the VIB t1 and RefineNet d3 transposed convs
 // (measured 3-18% faster than split A/B rings; the 64-column convs with the
 // TMA-store epilogue keep split rings, which fit two CTAs per SM).
-template <int BN, int CK, int TS> struct HaloGrpCfg {
-    static constexpr uint32_t A = (130 * CK * 2 + 1023) & ~1023u, G = A + ((3 * BN * CK * 2 + 1023) & ~1023u);
+template <int BN, int CK, int TS, int F8 = 0> struct HaloGrpCfg {
+    static constexpr uint32_t ES = F8 ? 1 : 2;
+    static constexpr uint32_t A = (130 * CK * ES + 1023) & ~1023u, G = A + ((3 * BN * CK * ES + 1023) & ~1023u);
     static constexpr uint32_t STG = stg_bytes(BN, TS);
     static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / G); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 2 ? ctas_for(c - 1) : c; }
@@ -1018,11 +1020,11 @@ template <int BN, int CK, int TS> struct HaloGrpCfg {
     static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "grouped halo config");
 };
 
-template <int BN, int CK, int TS>
+template <int BN, int CK, int TS, int F8 = 0>
 int launch_halo_grp(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                     cudaStream_t st) {
-    using C = HaloGrpCfg<BN, CK, TS>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 1, 2, TS, 0, 1>;
+    using C = HaloGrpCfg<BN, CK, TS, F8>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, TS, 0, 1>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1091,7 +1093,7 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap 
 constexpr int kHaloMT256 = 1;
 
 bool halo_ok(int bn, int ck, int es, bool f8) {
-    if (ck * es == 128) return f8 ? bn == 256 : (bn == 32 || bn == 64 || bn == 128 || bn == 256);
+    if (ck * es == 128) return f8 ? (bn == 256 || bn == 32) : (bn == 32 || bn == 64 || bn == 128 || bn == 256);
     return !f8 && ((bn == 16 && ck == 16) || (bn == 32 && ck == 32));
 }
 
@@ -1100,7 +1102,9 @@ bool halo_ok(int bn, int ck, int es, bool f8) {
 template <int TS>
 int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
                      const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
-    if (f8) return launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
+    if (f8) // the 256-channel convs as cluster pairs; the all-phase t1 (N = 32) on grouped stages
+        return bn == 32 ? launch_halo_grp<32, 128, TS, 1>(ma, mb3, mc, p, st)
+                        : launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
     if (ck == 16) return launch_halo_grp<16, 16, TS>(ma, mb3, mc, p, st);
     if (ck == 32) return launch_halo_grp<32, 32, TS>(ma, mb3, mc, p, st);
     switch (bn) {
@@ -1177,6 +1181,7 @@ int dispatch_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMa
     if (f8) {
         if (bn == 256 && ck == 128) return launch_cfg<256, 128, 1, TS>(ma, mb, mc, p, st);
         if (bn == 128 && ck == 128) return launch_cfg<128, 128, 1, TS>(ma, mb, mc, p, st);
+        if (bn == 32 && ck == 128) return launch_cfg<32, 128, 1, TS>(ma, mb, mc, p, st);
         set_error("no FP8 tensor-core kernel for N=%d, CK=%d", bn, ck);
         return FVV_EINVAL;
     }
@@ -1286,44 +1291,66 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         const float *w = blob + off;
         off += (size_t)L.ci * L.co * (L.kind == K_CONV ? 9 : 16) + L.co;
         if (!fp8_layer(i)) continue;
-        const bool conv = L.kind == K_CONV;
-        const int taps = conv ? 9 : 16; // conv taps, or phase x tap of the transposed conv
+        const bool conv = L.kind == K_CONV, t3 = tc_all_phases(i);
+        // conv taps, the all-phase transposed conv's 3x3 taps, or phase x tap slices
+        const int taps = conv || t3 ? 9 : 16;
+        const int rows = t3 ? pad16(4 * L.co) : L.co; // weight rows = GEMM columns
         // kernel value of (output channel, input channel, kernel position): conv
         // weights are [C_out][C_in][3][3], transposed-conv weights [C_in][C_out][4][4]
         auto wv = [&](int co, int ci, int k) {
             return conv ? w[((size_t)co * L.ci + ci) * 9 + k] : w[((size_t)ci * L.co + co) * 16 + k];
         };
         std::vector<float> sw(L.co);
-        std::vector<uint8_t> pk((size_t)taps * L.co * L.ci);
+        std::vector<uint8_t> pk((size_t)taps * rows * L.ci, 0); // 0 = the E4M3 code of +0
         for (int co = 0; co < L.co; ++co) {
             float m = 0.f;
             for (int ci = 0; ci < L.ci; ++ci)
                 for (int k = 0; k < (conv ? 9 : 16); ++k) m = fmaxf(m, fabsf(wv(co, ci, k)));
             sw[co] = m > 0.f ? m / 448.f : 1.f;
         }
-        for (int g = 0; g < taps; ++g) {
-            // transposed conv slice g = phase (py, px) x tap (ty, tx): kernel row
-            // 1 + 2 ty (py = 0) or 2 ty (py = 1), the same for columns
-            const int py = g >> 3, px = (g >> 2) & 1, ty = (g >> 1) & 1, tx = g & 1;
-            const int k = conv ? g : (py == 0 ? 1 + 2 * ty : 2 * ty) * 4 + (px == 0 ? 1 + 2 * tx : 2 * tx);
-            for (int co = 0; co < L.co; ++co)
-                for (int ci = 0; ci < L.ci; ++ci)
-                    pk[((size_t)g * L.co + co) * L.ci + ci] =
-                        (uint8_t)__nv_cvt_float_to_fp8(wv(co, ci, k) / sw[co], __NV_SATFINITE, __NV_E4M3);
+        auto code = [&](int co, int ci, int k) {
+            return (uint8_t)__nv_cvt_float_to_fp8(wv(co, ci, k) / sw[co], __NV_SATFINITE, __NV_E4M3);
+        };
+        if (t3) {
+            // all phases: 3x3 tap (dy, dx) of phase (py, px) in column ph * C_out + co, the
+            // same kernel positions as the BF16 packing; the 5 taps a phase skips stay 0
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int py = 0; py < 2; ++py)
+                        for (int px = 0; px < 2; ++px) {
+                            if (!(py == 0 ? dy <= 0 : dy >= 0) || !(px == 0 ? dx <= 0 : dx >= 0)) continue;
+                            const int ky = py == 0 ? (dy == 0 ? 1 : 3) : (dy == 1 ? 0 : 2);
+                            const int kx = px == 0 ? (dx == 0 ? 1 : 3) : (dx == 1 ? 0 : 2);
+                            const int tap = (dy + 1) * 3 + (dx + 1), ph = py * 2 + px;
+                            for (int co = 0; co < L.co; ++co)
+                                for (int ci = 0; ci < L.ci; ++ci)
+                                    pk[((size_t)tap * rows + ph * L.co + co) * L.ci + ci] = code(co, ci, ky * 4 + kx);
+                        }
+        } else {
+            for (int g = 0; g < taps; ++g) {
+                // transposed conv slice g = phase (py, px) x tap (ty, tx): kernel row
+                // 1 + 2 ty (py = 0) or 2 ty (py = 1), the same for columns
+                const int py = g >> 3, px = (g >> 2) & 1, ty = (g >> 1) & 1, tx = g & 1;
+                const int k = conv ? g : (py == 0 ? 1 + 2 * ty : 2 * ty) * 4 + (px == 0 ? 1 + 2 * tx : 2 * tx);
+                for (int co = 0; co < L.co; ++co)
+                    for (int ci = 0; ci < L.ci; ++ci) pk[((size_t)g * rows + co) * L.ci + ci] = code(co, ci, k);
+            }
         }
         TcWeights &tw = h->tc8[i];
         tw.ci_pad = L.ci;
-        tw.co_pad = L.co;
+        tw.co_pad = rows;
         FVV_TRY(dalloc(h, &tw.w, pk.size()));
         FVV_CHECK_CUDA(cudaMemcpy(tw.w, pk.data(), pk.size(), cudaMemcpyHostToDevice));
         FVV_TRY(dalloc(h, (void **)&h->q_acc[i], L.co * sizeof(float)));
         h->s_w[i] = sw;
-        cuuint64_t dims[3] = {(cuuint64_t)L.ci, (cuuint64_t)L.co, (cuuint64_t)taps};
-        cuuint64_t strides[2] = {(cuuint64_t)L.ci, (cuuint64_t)L.ci * L.co};
-        cuuint32_t box[3] = {128, (cuuint32_t)L.co, 1};
+        cuuint64_t dims[3] = {(cuuint64_t)L.ci, (cuuint64_t)rows, (cuuint64_t)taps};
+        cuuint64_t strides[2] = {(cuuint64_t)L.ci, (cuuint64_t)L.ci * rows};
+        cuuint32_t box[3] = {128, (cuuint32_t)rows, 3}; // three consecutive taps (grouped stages)
         g_encode_u8 = true;
-        int rc = encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, 128);
-        box[1] = (cuuint32_t)(L.co / 2);
+        int rc = taps == 9 ? encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, 128) : FVV_OK;
+        box[2] = 1;
+        if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, 128);
+        box[1] = (cuuint32_t)(rows / 2);
         if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, 128);
         g_encode_u8 = false;
         FVV_TRY(rc);

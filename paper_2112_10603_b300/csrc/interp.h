@@ -118,8 +118,9 @@ int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, in
             void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
 // FP8 layers: every VIBlock conv with 128 or 256 input channels -- c1 (128 -> 256,
-// stride 2), the six 256 -> 256 convs m0-m5 and t0 (256 -> 128 transposed); their
-// producers are the layer before (c0, c1, m0 .. m5) and write E4M3 codes.
-inline bool fp8_layer(int li) { return li < kCtx && li % 10 >= 1 && li % 10 <= 8; }
-inline bool feeds_fp8(int li) { return li < kCtx && li % 10 <= 7; }
+// stride 2), the six 256 -> 256 convs m0-m5, t0 (256 -> 128 transposed) and t1 (128 -> 5
+// transposed, all phases); their producers are the layer before (c0 .. t0) and write
+// E4M3 codes.
+inline bool fp8_layer(int li) { return li < kCtx && li % 10 >= 1; }
+inline bool feeds_fp8(int li) { return li < kCtx && li % 10 <= 8; }
 } // namespace fvv

@@ -1,6 +1,6 @@
 """FP8 (E4M3) path: every VIBlock conv with 128 or 256 input channels (c1, the six
-256-channel convs m0-m5, the transposed t0) with per-output-channel weight scales and
-calibrated per-tensor activation scales, FP32 accumulation.
+256-channel convs m0-m5, the transposed t0 and t1) with per-output-channel weight scales
+and calibrated per-tensor activation scales, FP32 accumulation.
 
 Kernel level: an FP8 layer on E4M3 input codes equals the oracle's conv of the
 dequantised operands (codes x scales): a product of two E4M3 values is exact in
@@ -78,10 +78,11 @@ def test_fp8_layer_matches_dequantised_oracle(torch_cuda, name, h, ww):
         assert np.abs(got[i] - ref).max() <= 1e-4 * scale
 
 
-@pytest.mark.parametrize("name", ["vib2.c1", "vib0.c1", "vib1.t0", "vib2.t0"])
+@pytest.mark.parametrize("name", ["vib2.c1", "vib0.c1", "vib1.t0", "vib2.t0", "vib2.t1", "vib0.t1"])
 def test_fp8_strided_and_transposed_layers(torch_cuda, name):
-    """The stride-2 c1 (128 -> 256) and the transposed t0 (256 -> 128) on E4M3 codes
-    equal the oracle's conv of the dequantised operands, ragged tiles included."""
+    """The stride-2 c1 (128 -> 256), the transposed t0 (256 -> 128) and the all-phase
+    transposed t1 (128 -> 5) on E4M3 codes equal the oracle's conv of the dequantised
+    operands, ragged tiles included."""
     torch = torch_cuda
     H, W = 64, 96
     it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=3)
