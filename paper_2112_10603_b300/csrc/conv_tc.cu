@@ -12,7 +12,11 @@
 //     (5-D map), so tap (ky, kx) is a plain box at (pair column ox-1 or ox,
 //     half = kx!=1, row pair oy-1 or oy, row parity = ky!=1);
 //   * 4x4 stride-2 transposed conv: 4 output phases, each a 2x2-tap conv on the
-//     input grid (phase p: taps read rows q - t (p=0) or q + 1 - t (p=1)).
+//     input grid (phase p: taps read rows q - t (p=0) or q + 1 - t (p=1)); with few
+//     output channels all 4 phases at once as one 3x3 conv (MODE_T3, N = 4 C_out);
+//   * E4M3 operands (kind::f8f6f4, K = 32 per MMA) for the FP8 layers.
+// Halo tiles, grouped stages, cluster pairs, the stride-2 pair halo and the TMA-store
+// epilogue are described at the kernel template below.
 // Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer (+ TMEM owner),
 // warps 2-5 = epilogue (TMEM -> registers -> bias, ReLU, BF16/FP32 -> global).
 // The accumulator is double-buffered in TMEM so the epilogue of one tile runs
@@ -385,7 +389,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                          y0 - (ky == 0 ? 1 : 0), n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
                     } else {
-                        // K order (channel block, tap): the same as the transposed-conv halo path
+                        // K order (channel block, tap)
                         tap = kb & 3;
                         c0 = (kb >> 2) * CK;
                         int py = ph >> 1, px = ph & 1, ty = tap >> 1, tx = tap & 1;
