@@ -153,6 +153,8 @@ template <int BN, int MT> struct AccCfg {
 // rings, halving the weight traffic from L2.  A slot of the B ring is released by
 // both CTAs' MMA commits; tiles go in pairs (a pair's odd last member is computed
 // on a clamped tile and not stored).
+// GRP = 2: the same with the nine weight slices of a one-block layer resident in shared
+// memory (loaded once per CTA); a stage is the A box alone.
 // GRP = 1 (halo, small N): one stage holds a (row tap, channel block)'s A box AND its
 // three weight slices, so the MMA thread syncs once per 3 x (row bytes / 32) MMAs.
 // S2H = 1 (stride-2 3x3 conv whose input pixel is one channel block of 16 or 32 channels):
@@ -184,7 +186,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr uint32_t BR_STRIDE = (9 * B_BYTES + 1023) & ~1023u; // S2H: the resident weight slices
     // grouped stage: A box + the row tap's 3 weight slices, loaded as ONE box of 3 taps
     // (slice kx at kx * B_BYTES; every B_BYTES here is a multiple of the swizzle atom)
-    constexpr uint32_t G_STRIDE = A_STRIDE + ((3 * B_BYTES + 1023) & ~1023u);
+    constexpr uint32_t G_STRIDE = GRP == 2 ? A_STRIDE : A_STRIDE + ((3 * B_BYTES + 1023) & ~1023u);
     constexpr int ACCB = AccCfg<BN, MT>::ACCB;
     constexpr uint32_t TMEM_COLS = AccCfg<BN, MT>::TMEM_COLS;
     constexpr uint32_t IDESC = F8 ? ptx::make_idesc(128, BN, 0, 0) : ptx::make_idesc(128, BN, 1, 1);
@@ -198,7 +200,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // staging buffers per epilogue warp: two (a chunk is staged while the previous one's
     // store reads), one for the two-row-block tiles, whose operand stages are larger
     constexpr int NSB = MT == 2 ? 1 : 2;
-    uint8_t *stg = sB + (GRP ? 0u : (S2H ? BR_STRIDE : (HALO ? STAGES_B : STAGES) * B_STRIDE));
+    uint8_t *stg = sB + (GRP == 1 ? 0u : (S2H || GRP == 2 ? BR_STRIDE : (HALO ? STAGES_B : STAGES) * B_STRIDE));
     Bars *bars = (Bars *)(stg + (TS ? 4 * NSB * STG_BYTES : 0));
     volatile int *abort = &bars->abort;
 
@@ -207,7 +209,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (threadIdx.x == 0) {
         // halo: full/empty[0, STAGES) = A ring, [STAGES, STAGES + STAGES_B) = B ring
         // S2H: full[STAGES] = the resident weights
-        for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES + S2H); ++s) {
+        for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES + (S2H || GRP == 2 ? 1 : 0)); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), MC && s >= STAGES ? 2 : 1);
         }
@@ -276,6 +278,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
         } else if (lane == 0 && GRP) {
+            const uint32_t fw = ptx::smem_u32(&bars->full[STAGES]); // GRP == 2: resident weights
+            if (GRP == 2) {
+                ptx::mbar_arrive_expect_tx(fw, 9 * B_BYTES);
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky) // taps 3ky .. 3ky + 2 per box
+                    ptx::tma_load_3d(ptx::smem_u32(sB) + ky * 3 * B_BYTES, &tmB, fw, 0, 0, ky * 3);
+            }
             int s = 0;
             uint32_t ph_bit = 0;
             long long issued = 0;
@@ -287,16 +296,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     for (int c = 0; c < p.nck; ++c) {
                         if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
                         const uint32_t fs = ptx::smem_u32(&bars->full[s]);
-                        ptx::mbar_arrive_expect_tx(fs, A_BYTES + 3 * B_BYTES);
+                        ptx::mbar_arrive_expect_tx(fs, GRP == 2 ? A_BYTES : A_BYTES + 3 * B_BYTES);
                         const uint32_t base = ptx::smem_u32(sA + s * G_STRIDE);
                         ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
-                        ptx::tma_load_3d(base + A_STRIDE, &tmB, fs, c * CK, 0, ky * 3); // taps ky*3 .. ky*3+2
+                        if (GRP == 1)
+                            ptx::tma_load_3d(base + A_STRIDE, &tmB, fs, c * CK, 0, ky * 3); // taps ky*3 .. ky*3+2
                         ++issued;
                         if (++s == STAGES) { s = 0; ph_bit ^= 1; }
                     }
             }
             if (*abort || stop) {
                 // let every copy still in flight land before the CTA exits
+                if (GRP == 2) {
+                    long long t0 = clock64();
+                    while (!ptx::mbar_try_wait(fw, 0) && clock64() - t0 < kWaitCycles) {}
+                }
                 for (int i = 0; i < STAGES && i < issued; ++i) {
                     long long k = issued - 1 - i;
                     long long t0 = clock64();
@@ -464,7 +478,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            // GRP == 2: the resident weight slices (one channel block: group g = row tap ky)
+            const bool wok = GRP != 2 || wait_bar(ptx::smem_u32(&bars->full[STAGES]), 0, abort, p.err, 3);
+            ptx::tc_fence_after();
+            for (int t = blockIdx.x; wok && t < p.num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem + acc * (MT * BN);
@@ -476,7 +493,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const uint32_t a0 = ptx::smem_u32(sA + s * G_STRIDE);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx) {
-                        const uint32_t b0 = a0 + A_STRIDE + kx * B_BYTES;
+                        const uint32_t b0 = GRP == 2 ? ptx::smem_u32(sB) + (g * 3 + kx) * B_BYTES
+                                                     : a0 + A_STRIDE + kx * B_BYTES;
 #pragma unroll
                         for (int k = 0; k < ROW_BYTES / 32; ++k) {
                             uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
@@ -1012,23 +1030,26 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
 // layers: the narrow 16/32-channel convs, the VIB t1 and RefineNet d3 transposed convs
 // (measured 3-18% faster than split A/B rings; the 64-column convs with the
 // TMA-store epilogue keep split rings, which fit two CTAs per SM).
-template <int BN, int CK, int TS, int F8 = 0> struct HaloGrpCfg {
+// RES = 1: the nine weight slices of a one-block layer resident (BR bytes), stages hold A only.
+template <int BN, int CK, int TS, int F8 = 0, int RES = 0> struct HaloGrpCfg {
     static constexpr uint32_t ES = F8 ? 1 : 2;
-    static constexpr uint32_t A = (130 * CK * ES + 1023) & ~1023u, G = A + ((3 * BN * CK * ES + 1023) & ~1023u);
+    static constexpr uint32_t A = (130 * CK * ES + 1023) & ~1023u;
+    static constexpr uint32_t G = RES ? A : A + ((3 * BN * CK * ES + 1023) & ~1023u);
+    static constexpr uint32_t BR = RES ? ((9 * BN * CK * ES + 1023) & ~1023u) : 0u;
     static constexpr uint32_t STG = stg_bytes(BN, TS);
-    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG) / G); }
+    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - STG - BR) / G); }
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 2 ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for(BN <= 32 ? 3 : 2);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * G + STG + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * G + BR + STG + sizeof(Bars) + 1024;
     static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "grouped halo config");
 };
 
-template <int BN, int CK, int TS, int F8 = 0>
+template <int BN, int CK, int TS, int F8 = 0, int RES = 0>
 int launch_halo_grp(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                     cudaStream_t st) {
-    using C = HaloGrpCfg<BN, CK, TS, F8>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, TS, 0, 1>;
+    using C = HaloGrpCfg<BN, CK, TS, F8, RES>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, TS, 0, RES ? 2 : 1>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1109,8 +1130,9 @@ int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUten
     if (f8) // the 256-channel convs as cluster pairs; the all-phase t1 (N = 32) on grouped stages
         return bn == 32 ? launch_halo_grp<32, 128, TS, 1>(ma, mb3, mc, p, st)
                         : launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
-    if (ck == 16) return launch_halo_grp<16, 16, TS>(ma, mb3, mc, p, st);
-    if (ck == 32) return launch_halo_grp<32, 32, TS>(ma, mb3, mc, p, st);
+    // the 16 / 32-channel convs (one channel block): weight slices resident
+    if (ck == 16) return launch_halo_grp<16, 16, TS, 0, 1>(ma, mb3, mc, p, st);
+    if (ck == 32) return launch_halo_grp<32, 32, TS, 0, 1>(ma, mb3, mc, p, st);
     switch (bn) {
     case 32: return launch_halo_grp<32, 64, TS>(ma, mb3, mc, p, st);
     case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb3, mc, p, st)
