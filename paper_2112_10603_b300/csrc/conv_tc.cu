@@ -1135,7 +1135,7 @@ int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUten
     if (ck == 32) return launch_halo_grp<32, 32, TS, 0, 1>(ma, mb3, mc, p, st);
     switch (bn) {
     case 32: return launch_halo_grp<32, 64, TS>(ma, mb3, mc, p, st);
-    case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0>(ma, mb3, mc, p, st)
+    case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0, 0, 1>(ma, mb3, mc, p, st)
                                              : launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
     case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
     default: return launch_halo<256, 0, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
