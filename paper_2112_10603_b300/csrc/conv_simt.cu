@@ -218,107 +218,7 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
     store16(dst, o);
 }
 
-// RefineNet's last layer (Conv2d 16 -> 3, then Sigmoid, Table 3) fused with the
-// residual output: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped.  Only
-// 3 output channels: a tensor-core tile would use 3 of its 16 columns, so this is
-// a shared-memory-tiled direct conv.  A block computes 32 x 32 output pixels of one
-// view from a (32 + 2) x (32 + 2) input patch (16 bf16 channels per pixel, stored
-// with a 9-word pitch so that neighbouring pixels fall in different banks).  Each
-// thread owns a column of 4 output rows: every input value it loads (6 rows x 3
-// columns per channel pair) feeds up to 3 of them, and each channel pair's 54
-// weights are loaded once for the 4 outputs.
-constexpr int OC_TX = 32, OC_TY = 8, OC_RPT = 4, OC_PITCH = 9; // OC_PITCH: words per pixel
-constexpr int OC_ROWS = OC_TY * OC_RPT;                          // output rows per block
-
-// Channels are taken in pairs (2 c2, 2 c2 + 1): one packed FP32x2 FMA updates the
-// even- and odd-channel partial sums of an output channel at once; the two partials
-// are added after the last pair.  Weights in shared memory: per channel pair 27 float2
-// (tap, output channel) = (w[tap][2 c2][co], w[tap][2 c2 + 1][co]), padded to 14 float4.
-// Four blocks per SM (64 registers) measured faster than three with 74.
-__global__ void __launch_bounds__(OC_TX *OC_TY, 4)
-out_conv_fused_kernel(const bf16 *in, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
-                      float *const *outp, int H, int W) {
-    __shared__ uint32_t tile[(OC_ROWS + 2) * (OC_TX + 2) * OC_PITCH];
-    __shared__ float4 ws[8 * 14];
-    __shared__ float bs[3];
-    const int tid = threadIdx.x, n = blockIdx.z;
-    const int x0 = blockIdx.x * OC_TX, y0 = blockIdx.y * OC_ROWS;
-    for (int i = tid; i < 8 * 28; i += blockDim.x) {
-        const int c2 = i / 28, k = i % 28, tap = k / 3, co = k % 3;
-        float2 w2 = make_float2(0.f, 0.f);
-        if (k < 27) w2 = make_float2(wp[(tap * 16 + 2 * c2) * 3 + co], wp[(tap * 16 + 2 * c2 + 1) * 3 + co]);
-        reinterpret_cast<float2 *>(ws)[i] = w2;
-    }
-    if (tid < 3) bs[tid] = bias[tid];
-    const int npx = (OC_ROWS + 2) * (OC_TX + 2);
-    for (int i = tid; i < npx * 2; i += blockDim.x) {
-        int p = i >> 1, half = i & 1;
-        int iy = y0 - 1 + p / (OC_TX + 2), ix = x0 - 1 + p % (OC_TX + 2);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (iy >= 0 && iy < Hp && ix >= 0 && ix < Wp)
-            v = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)n * Hp + iy) * Wp + ix) * 16) + half);
-        uint32_t *d = tile + p * OC_PITCH + half * 4;
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-    }
-    __syncthreads();
-    const int tx = tid % OC_TX, ty = tid / OC_TX;
-    const int ox = x0 + tx, oy0 = y0 + ty * OC_RPT;
-    if (ox >= W || oy0 >= H) return;
-    float2 acc[OC_RPT][3]; // (even-channel, odd-channel) partial sums
-#pragma unroll
-    for (int j = 0; j < OC_RPT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = make_float2(0.f, 0.f);
-    const uint32_t *col = tile + (ty * OC_RPT * (OC_TX + 2) + tx) * OC_PITCH;
-#pragma unroll 1
-    for (int c2 = 0; c2 < 8; ++c2) {
-        float2 w[28]; // (tap, co) -> (channel 2 c2, channel 2 c2 + 1)
-#pragma unroll
-        for (int q = 0; q < 14; ++q) {
-            const float4 f = ws[c2 * 14 + q];
-            w[2 * q] = make_float2(f.x, f.y);
-            w[2 * q + 1] = make_float2(f.z, f.w);
-        }
-#pragma unroll
-        for (int r = 0; r < OC_RPT + 2; ++r)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                __nv_bfloat162 hv;
-                memcpy(&hv, col + (r * (OC_TX + 2) + dx) * OC_PITCH + c2, 4);
-                const float2 v = __bfloat1622float2(hv);
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    const int j = r - dy;
-                    if (j < 0 || j >= OC_RPT) continue;
-#pragma unroll
-                    for (int co = 0; co < 3; ++co) acc[j][co] = __ffma2_rn(v, w[(dy * 3 + dx) * 3 + co], acc[j][co]);
-                }
-            }
-    }
-    float *out = *outp;
-#pragma unroll
-    for (int j = 0; j < OC_RPT; ++j) {
-        const int oy = oy0 + j;
-        if (oy >= H) break;
-        const size_t q = ((size_t)n * Hp + oy) * Wp + ox;
-        float *o = out + (((size_t)n * H + oy) * W + ox) * 3;
-#pragma unroll
-        for (int co = 0; co < 3; ++co) {
-            float z = acc[j][co].x + acc[j][co].y + bs[co];
-            float r = 2.f / (1.f + expf(-z)) - 1.f;
-            o[co] = fminf(fmaxf(__ldg(ib + q * 3 + co) + r, 0.f), 1.f);
-        }
-    }
-}
-
 } // namespace
-
-int launch_out_conv_fused(const bf16 *in, int N, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
-                          float *const *outp, int H, int W, cudaStream_t st) {
-    dim3 grid(ceil_div(W, OC_TX), ceil_div(H, OC_ROWS), N);
-    out_conv_fused_kernel<<<grid, OC_TX * OC_TY, 0, st>>>(in, Hp, Wp, wp, bias, ib, outp, H, W);
-    count_launch();
-    FVV_CHECK_CUDA(cudaGetLastError());
-    return FVV_OK;
-}
 
 int launch_conv_c3(const ConvArgs &a, bool out_bf16, cudaStream_t st) {
     if (a.Ci != 3 || a.Co != 16 || a.kind != K_CONV) { set_error("conv_c3: 3 -> 16 conv only"); return FVV_EINVAL; }

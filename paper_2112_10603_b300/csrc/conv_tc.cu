@@ -624,6 +624,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * NSB * STG_BYTES);
         const int tw = 1 << p.tw_log;
         const int dy = row >> p.tw_log, dx = row & (tw - 1);
+        // fused network output (N = 16 tiles): the cropped output buffer
+        float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
         for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
             const bool phantom = t >= p.num_tiles; // pair filler: computed, never stored
@@ -826,6 +828,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int co0 = p.mode == MODE_T3 ? c - cph * p.co : c;
                 int oy = gy, ox = gx;
                 if (p.mode == MODE_T || p.mode == MODE_T3) { oy = 2 * gy + (cph >> 1); ox = 2 * gx + (cph & 1); }
+                if (BN == 16 && p.epi.mode == EPI_OUTPUT) {
+                    // RefineNet's 16 -> 3 output conv (Sigmoid, Table 3) with the residual
+                    // output: clamp(I_blend + 2 sigmoid(z) - 1, 0, 1) on the cropped grid
+                    if (oy < p.epi.crop_h && ox < p.epi.crop_w) {
+                        const size_t q = ((size_t)n * p.out_h + oy) * p.out_w + ox;
+                        float *o = out_final + (((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const float z = __uint_as_float(r[j]) + __ldg(p.bias + j);
+                            const float res = 2.f / (1.f + expf(-z)) - 1.f;
+                            o[j] = fminf(fmaxf(__ldg(p.epi.ib + q * 3 + j) + res, 0.f), 1.f);
+                        }
+                    }
+                    continue;
+                }
                 if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co) {
                     float v[16];
                     float vmax = 0.f;
@@ -1451,7 +1468,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them
         bool ok = (epi->mode == EPI_STORE) ||
-                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5);
+                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5) ||
+                  (epi->mode == EPI_OUTPUT && p.mode == MODE_S1 && L.co == 3 && bn == 16 && !f8 && epi->ib &&
+                   epi->final_out_ref && epi->crop_h <= p.gh && epi->crop_w <= p.gw);
         if (!ok) { set_error("layer %s: unsupported fused epilogue", L.name); return FVV_EINVAL; }
     }
 

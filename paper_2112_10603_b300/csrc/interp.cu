@@ -122,15 +122,11 @@ static int conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, i
 static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
                      void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi) {
     const LayerDef &L = kLayers[li];
-    // the 16 -> 3 output conv with the fused residual output: 3 useful columns of a
-    // 16-wide tensor-core tile do not pay; a tiled direct kernel does the job
-    if (epi && epi->mode == EPI_OUTPUT) {
-        if (!is_bf16(h) || li != kRef + 12 || in_cs != 16 || in_coff != 0) {
-            set_error("the fused residual output runs on the bf16 16 -> 3 output conv only");
-            return FVV_EINVAL;
-        }
-        return launch_out_conv_fused((const bf16 *)in, N, Hin, Win, h->w32 + h->w_off[li], h->bias + h->b_off[li],
-                                     epi->ib, epi->final_out_ref, epi->crop_h, epi->crop_w, st);
+    // the 16 -> 3 output conv with the fused residual output: an N = 16 tensor-core
+    // tile (3 useful columns) whose epilogue writes the cropped output
+    if (epi && epi->mode == EPI_OUTPUT && (!is_bf16(h) || li != kRef + 12 || in_cs != 16 || in_coff != 0)) {
+        set_error("the fused residual output runs on the bf16 16 -> 3 output conv only");
+        return FVV_EINVAL;
     }
     // ContextNet's first layer reads the 3-channel FP32 frame: SIMT on every path
     const bool simt = !is_bf16(h) || li == kCtx;

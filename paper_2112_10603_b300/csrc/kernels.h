@@ -15,10 +15,6 @@ struct ViewTab {
 int launch_conv_simt(const ConvArgs &a, bool in_bf16, bool out_bf16, cudaStream_t st);
 // direct kernel for a 3 -> 16 channel conv read from FP32 (ContextNet's first layer)
 int launch_conv_c3(const ConvArgs &a, bool out_bf16, cudaStream_t st);
-// RefineNet's 16 -> 3 output conv (bf16 input, 16-channel pixels) fused with the
-// residual output clamp(I_blend + 2 sigmoid(z) - 1, 0, 1) and the crop to H x W
-int launch_out_conv_fused(const bf16 *in, int N, int Hp, int Wp, const float *wp, const float *bias, const float *ib,
-                          float *const *outp, int H, int W, cudaStream_t st);
 void pack_simt(int kind, int Ci, int Co, const float *w, float *dst);
 
 // Frame pyramid levels (img0 = padded frame, img1 = 1/2, img2 = 1/4 box levels):

@@ -33,10 +33,11 @@ from tests.gpu_common import blob, pair
 
 pytestmark = pytest.mark.gpu
 
-# 128-byte rows (C_in >= 64), the narrow 32- / 64-byte rows (C_in = 16, 32) and the
-# all-phase transposed convs (t1, d3, and d2 with TMA-stored phases)
+# 128-byte rows (C_in >= 64), the narrow 32- / 64-byte rows (C_in = 16, 32; ref.out: an
+# N = 16 tile with 3 real columns) and the all-phase transposed convs (t1, d3, and d2
+# with TMA-stored phases)
 HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3", "ctx.c1", "ctx.c3",
-               "ref.e0b", "ref.d2"]
+               "ref.e0b", "ref.d2", "ref.out"]
 
 
 @pytest.fixture(scope="module")
