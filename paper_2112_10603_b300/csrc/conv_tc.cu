@@ -66,7 +66,19 @@ struct TcParams {
     float out_q;
     float *amax;            // calibration: running max |output| (NULL: off)
     int tma_store;          // epilogue stages each warp's 32 rows in shared memory, TMA stores them
+    int kxf;                // column taps folded into N: tiles of kKxfTile output pixels of one row
 };
+
+// Column taps folded into N (3x3 stride-1 convs and the all-phase transposed convs with
+// few output channels): the weight slice of row tap ky holds the three column taps
+// side by side (N = 3 G, G = output columns per tap), so ONE MMA per K step covers all
+// three and the A operand is fetched a third as often.  Row r of the accumulator is then
+// the partial sum of input pixel r for every column tap; output pixel r sums tap 0 of
+// row r - 1, tap 1 of row r and tap 2 of row r + 1 -- neighbouring TMEM lanes, i.e.
+// neighbouring threads of an epilogue warp (warp shuffles).  Each warp's 32 rows are
+// loaded as their own box of 32 input pixels, overlapping the next warp's by 2, so a
+// warp never needs another warp's rows: lanes 1..30 produce outputs, 120 per tile.
+constexpr int kKxfTile = 120;
 
 __device__ __forceinline__ uint8_t to_e4m3(float v) {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
@@ -104,7 +116,75 @@ __device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase
     int ty = r % p.tiles_y;
     n = r / p.tiles_y;
     y0 = ty << p.th_log;
-    x0 = tx << p.tw_log;
+    x0 = p.kxf ? tx * kKxfTile : tx << p.tw_log;
+}
+
+// Eq. 2 update of a 4-phase transposed conv with 5 outputs (the VIB t1 layer): the
+// pixel (gy, gx) of the half grid owns the 4 fine pixels (2 gy + py, 2 gx + px); their
+// x2 upsampling reads the 3x3 neighbourhood of (gy, gx) in the previous stage's F, M,
+// fetched into nb before the accumulator is ready.  row32: the warp's lanes hold 32
+// consecutive pixels of one row (each lane loads its own column, neighbours by shuffle).
+__device__ __forceinline__ void resid_nb(const TcParams &p, int n, int gy, int gx, int lane, bool row32,
+                                         float (&nb)[3][3][5]) {
+    const int h2 = p.gh, w2 = p.gw;
+    const float *fm = p.epi.fm_prev + (size_t)n * h2 * w2 * 5;
+    if (row32) {
+        const int xc = min(max(gx, 0), w2 - 1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int yy = min(max(gy + a - 1, 0), h2 - 1);
+            const float *src = fm + ((size_t)yy * w2 + xc) * 5;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) nb[a][1][k] = __ldg(src + k);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                nb[a][0][k] = __shfl_up_sync(0xffffffffu, nb[a][1][k], 1);
+                nb[a][2][k] = __shfl_down_sync(0xffffffffu, nb[a][1][k], 1);
+            }
+        if (lane == 0 || lane == 31) {
+            const int b = lane == 0 ? 0 : 2;
+            const int xx = lane == 0 ? max(xc - 1, 0) : min(xc + 1, w2 - 1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int yy = min(max(gy + a - 1, 0), h2 - 1);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(fm + ((size_t)yy * w2 + xx) * 5 + k);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                int yy = min(max(gy + a - 1, 0), h2 - 1), xx = min(max(gx + b - 1, 0), w2 - 1);
+                const float *src = fm + ((size_t)yy * w2 + xx) * 5;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(src + k);
+            }
+    }
+}
+
+// F^s, M^s = up(F^{s-1}) x 2, up(M^{s-1}) + Res^s for accumulator column col (phase
+// col / 5, channel col % 5) of a pixel whose neighbourhood is nb
+__device__ __forceinline__ float resid_value(const float (&nb)[3][3][5], int col, float acc, float sc, float bias) {
+    const int pj = col / 5, co = col % 5, py = pj >> 1, px = pj & 1;
+    const float ly = py ? 0.25f : 0.75f, lx = px ? 0.25f : 0.75f;
+    float up = (1.f - ly) * ((1.f - lx) * nb[py][px][co] + lx * nb[py][px + 1][co]) +
+               ly * ((1.f - lx) * nb[py + 1][px][co] + lx * nb[py + 1][px + 1][co]);
+    return acc * sc + bias + up * (co < 4 ? 2.f : 1.f);
+}
+__device__ __forceinline__ float resid_value(const TcParams &p, const float (&nb)[3][3][5], int col, float acc) {
+    const int co = col % 5;
+    return resid_value(nb, col, acc, p.acc_scale ? __ldg(p.acc_scale + co) : 1.f, __ldg(p.bias + co));
+}
+__device__ __forceinline__ void resid_store(const TcParams &p, const float (&nb)[3][3][5], int n, int gy, int gx,
+                                            int col, float acc) {
+    const int pj = col / 5, co = col % 5, py = pj >> 1, px = pj & 1;
+    size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
+    ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = resid_value(p, nb, col, acc);
 }
 
 // One output element of the epilogue (scalar path): bias, ReLU, then store, or
@@ -164,14 +244,18 @@ template <int BN, int MT> struct AccCfg {
 // (descriptor start +1 row and/or + one pixel's bytes).  The nine weight slices stay
 // resident in shared memory (loaded once per CTA).  K order (ky, kx, k) as on the
 // per-tap path.
+// KXF = number of channel blocks (0: off): column taps folded into N (kKxfTile), on the
+// resident-weight grouped path (GRP = 2): a stage is the four 32-pixel boxes of one
+// (row tap, channel block), the weights are 3 x KXF folded slices of N rows.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0, int GRP = 0, int S2H = 0>
+          int MC = 0, int GRP = 0, int S2H = 0, int KXF = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     constexpr int ES = F8 ? 1 : 2;                 // operand element bytes
     constexpr int ROW_BYTES = CK * ES;
-    constexpr uint32_t A_BYTES = S2H ? 129 * 2 * ROW_BYTES : (HALO ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES),
+    constexpr uint32_t A_BYTES = S2H ? 129 * 2 * ROW_BYTES
+                                     : (HALO && !KXF ? 130 * MT * ROW_BYTES : 128 * MT * ROW_BYTES),
                        B_BYTES = BN * ROW_BYTES;
     constexpr int HROW = 130; // pixels per row of a halo box
     constexpr int NB = 3;     // weight slices (column taps) per halo box
@@ -183,7 +267,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     static_assert(!S2H || (!HALO && !MC && !GRP && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
                            (ROW_BYTES == 32 || ROW_BYTES == 64)),
                   "stride-2 pair halo: one 16/32-channel block, pair rows of 64/128 bytes");
-    constexpr uint32_t BR_STRIDE = (9 * B_BYTES + 1023) & ~1023u; // S2H: the resident weight slices
+    static_assert(!KXF || (GRP == 2 && MT == 1 && !TS && KXF <= 2), "folded column taps: resident grouped stages");
+    // S2H / GRP == 2: the resident weight slices (KXF: 3 folded slices per channel block)
+    constexpr uint32_t BR_STRIDE = ((KXF ? 3 * KXF : 9) * B_BYTES + 1023) & ~1023u;
     // grouped stage: A box + the row tap's 3 weight slices, loaded as ONE box of 3 taps
     // (slice kx at kx * B_BYTES; every B_BYTES here is a multiple of the swizzle atom)
     constexpr uint32_t G_STRIDE = GRP == 2 ? A_STRIDE : A_STRIDE + ((3 * B_BYTES + 1023) & ~1023u);
@@ -201,7 +287,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // store reads), one for the two-row-block tiles, whose operand stages are larger
     constexpr int NSB = MT == 2 ? 1 : 2;
     uint8_t *stg = sB + (GRP == 1 ? 0u : (S2H || GRP == 2 ? BR_STRIDE : (HALO ? STAGES_B : STAGES) * B_STRIDE));
-    Bars *bars = (Bars *)(stg + (TS ? 4 * NSB * STG_BYTES : 0));
+    // KXF: per epilogue warp the Eq. 2 outputs of its 30 pixels, two fine rows of 60 x 5
+    // floats, staged so that the warp stores whole rows
+    constexpr uint32_t KST_BYTES = KXF ? 4 * 2 * 300 * 4 : 0;
+    Bars *bars = (Bars *)(stg + (TS ? 4 * NSB * STG_BYTES : KST_BYTES));
     volatile int *abort = &bars->abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -279,7 +368,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
         } else if (lane == 0 && GRP) {
             const uint32_t fw = ptx::smem_u32(&bars->full[STAGES]); // GRP == 2: resident weights
-            if (GRP == 2) {
+            if (KXF) {
+                // channel block c: the folded slices of row taps 0..2 in one box
+                ptx::mbar_arrive_expect_tx(fw, 3 * KXF * B_BYTES);
+#pragma unroll
+                for (int c = 0; c < KXF; ++c)
+                    ptx::tma_load_3d(ptx::smem_u32(sB) + c * 3 * B_BYTES, &tmB, fw, c * CK, 0, 0);
+            } else if (GRP == 2) {
                 ptx::mbar_arrive_expect_tx(fw, 9 * B_BYTES);
 #pragma unroll
                 for (int ky = 0; ky < 3; ++ky) // taps 3ky .. 3ky + 2 per box
@@ -298,7 +393,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         const uint32_t fs = ptx::smem_u32(&bars->full[s]);
                         ptx::mbar_arrive_expect_tx(fs, GRP == 2 ? A_BYTES : A_BYTES + 3 * B_BYTES);
                         const uint32_t base = ptx::smem_u32(sA + s * G_STRIDE);
-                        ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
+                        if (KXF) { // epilogue warp q's rows: input pixels x0 - 1 + 30 q .. + 31
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                ptx::tma_load_4d(base + q * 32 * ROW_BYTES, &tmA, fs, p.in_coff + c * CK,
+                                                 x0 - 1 + 30 * q, y0 + ky - 1, n);
+                        } else {
+                            ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
+                        }
                         if (GRP == 1)
                             ptx::tma_load_3d(base + A_STRIDE, &tmB, fs, c * CK, 0, ky * 3); // taps ky*3 .. ky*3+2
                         ++issued;
@@ -491,8 +593,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     if (!wait_bar(ptx::smem_u32(&bars->full[s]), ph_bit, abort, p.err, 3)) { ok = false; break; }
                     ptx::tc_fence_after();
                     const uint32_t a0 = ptx::smem_u32(sA + s * G_STRIDE);
+                    if (KXF) {
+                        // the folded slice of (row tap ky, channel block c): all three column taps
+                        const int ky = g / KXF, c = g - ky * KXF;
+                        const uint32_t b0 = ptx::smem_u32(sB) + (c * 3 + ky) * B_BYTES;
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
+                        for (int k = 0; k < ROW_BYTES / 32; ++k) {
+                            const uint64_t bd = ptx::smem_desc(b0 + k * 32, ROW_BYTES);
+                            const uint64_t ad = ptx::smem_desc(a0 + k * 32, ROW_BYTES);
+                            if (F8) ptx::mma_f8(d, ad, bd, IDESC, accumulate | (uint32_t)k);
+                            else ptx::mma_bf16(d, ad, bd, IDESC, accumulate | (uint32_t)k);
+                        }
+                        accumulate = 1;
+                    }
+#pragma unroll
+                    for (int kx = 0; kx < (KXF ? 0 : 3); ++kx) {
                         const uint32_t b0 = GRP == 2 ? ptx::smem_u32(sB) + (g * 3 + kx) * B_BYTES
                                                      : a0 + A_STRIDE + kx * B_BYTES;
 #pragma unroll
@@ -624,6 +739,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t stg_warp = ptx::smem_u32(stg) + (uint32_t)(q * NSB * STG_BYTES);
         const int tw = 1 << p.tw_log;
         const int dy = row >> p.tw_log, dx = row & (tw - 1);
+        float *const kst = KXF ? (float *)stg + q * 600 : nullptr; // folded taps: Eq. 2 staging
+        float r_bias[5], r_sc[5]; // folded taps, Eq. 2: bias and dequantisation scale of F, M
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            r_bias[k] = KXF && p.epi.mode == EPI_RESID ? __ldg(p.bias + k) : 0.f;
+            r_sc[k] = KXF && p.epi.mode == EPI_RESID && p.acc_scale ? __ldg(p.acc_scale + k) : 1.f;
+        }
         // fused network output (N = 16 tiles): the cropped output buffer
         float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
         for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
@@ -633,53 +755,82 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int gy = y0 + dy, gx = x0 + dx;
             bool valid = gy < p.gh && gx < p.gw && !phantom;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
-            if (MT == 1 && BN == 32 && p.epi.mode == EPI_RESID) {
+            if (KXF) {
+                // folded column taps: this lane's row is input pixel x0 - 1 + 30 q + lane; lanes
+                // 1..30 sum tap 0 of the lane before, tap 1 of their own and tap 2 of the next
+                const int G = p.mode == MODE_T3 ? 4 * p.co : p.co; // accumulator columns per tap
+                const int kgx = x0 - 1 + 30 * q + lane;
+                const bool kvalid = lane >= 1 && lane <= 30 && kgx < p.gw && y0 < p.gh;
+                const bool resid = p.epi.mode == EPI_RESID;
+                float nb[3][3][5];
+                if (resid) resid_nb(p, n, y0, kgx, lane, true, nb);
+                if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
+                ptx::tc_fence_after();
+                // (j0 unrolled over the BN / 3 columns a tap can have: static register indices)
+#pragma unroll
+                for (int j0 = 0; j0 < BN / 3; j0 += 16) {
+                    if (j0 >= G) break;
+                    // 4-column loads: G is a multiple of 4, so every load starts on a
+                    // multiple of its own width
+                    uint32_t ra[16], rb[16], rc[16];
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4) {
+                        ra[u] = ra[u + 1] = ra[u + 2] = ra[u + 3] = 0u;
+                        rb[u] = rb[u + 1] = rb[u + 2] = rb[u + 3] = 0u;
+                        rc[u] = rc[u + 1] = rc[u + 2] = rc[u + 3] = 0u;
+                        if (j0 + u < G) {
+                            ptx::tmem_ld4(tbase + j0 + u, ra + u);
+                            ptx::tmem_ld4(tbase + G + j0 + u, rb + u);
+                            ptx::tmem_ld4(tbase + 2 * G + j0 + u, rc + u);
+                        }
+                    }
+                    ptx::tmem_ld_wait();
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float left = __shfl_up_sync(0xffffffffu, __uint_as_float(ra[j]), 1);
+                        const float right = __shfl_down_sync(0xffffffffu, __uint_as_float(rc[j]), 1);
+                        v[j] = left + __uint_as_float(rb[j]) + right;
+                    }
+                    if (!kvalid) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = j0 + j;
+                        if (col >= G) break;
+                        if (resid) {
+                            // fine pixel (2 y0 + py, 2 kgx + px), channel co -> staging row py
+                            const int pj = col / 5, co = col % 5;
+                            kst[(pj >> 1) * 300 + (2 * (lane - 1) + (pj & 1)) * 5 + co] =
+                                resid_value(nb, col, v[j], r_sc[co], r_bias[co]);
+                        } else if (p.mode == MODE_T3) {
+                            const int pj = col / p.co, co = col - pj * p.co;
+                            epi_elem(p, n, 2 * y0 + (pj >> 1), 2 * kgx + (pj & 1), co, v[j]);
+                        } else {
+                            epi_elem(p, n, y0, kgx, col, v[j]);
+                        }
+                    }
+                }
+                if (resid) {
+                    // the warp's two fine rows, 2 x 30 pixels x 5 channels each, as whole
+                    // 128-byte lines (F, M are dense: C = 5, no channel offset)
+                    __syncwarp();
+                    const int gx0 = x0 + 30 * q; // pixel of lane 1
+#pragma unroll
+                    for (int py = 0; py < 2; ++py) {
+                        float *dst = (float *)p.out + (((size_t)n * p.out_h + 2 * y0 + py) * p.out_w + 2 * gx0) * 5;
+                        for (int i = lane; i < 300; i += 32)
+                            if (2 * gx0 + i / 5 < p.out_w) dst[i] = kst[py * 300 + i];
+                    }
+                    __syncwarp();
+                }
+            } else if (MT == 1 && BN == 32 && p.epi.mode == EPI_RESID) {
                 // Eq. 2 update of a 4-phase transposed conv with 5 outputs (the VIB
                 // t1 layer): this pixel q of the half grid owns the 4 fine pixels
                 // (2q + phase); their x2 upsampling reads the 3x3 neighbourhood of q
                 // in the previous stage's F, M, fetched before the accumulator is ready.
                 float nb[3][3][5];
-                const int h2 = p.gh, w2 = p.gw;
-                const float *fm = p.epi.fm_prev + (size_t)n * h2 * w2 * 5;
-                if (p.tw_log >= 5) {
-                    // a warp covers 32 consecutive pixels of one row: each lane loads its
-                    // own column (coalesced) and takes its neighbours' by shuffle
-                    const int xc = min(gx, w2 - 1);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const int yy = min(max(gy + a - 1, 0), h2 - 1);
-                        const float *src = fm + ((size_t)yy * w2 + xc) * 5;
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) nb[a][1][k] = __ldg(src + k);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            nb[a][0][k] = __shfl_up_sync(0xffffffffu, nb[a][1][k], 1);
-                            nb[a][2][k] = __shfl_down_sync(0xffffffffu, nb[a][1][k], 1);
-                        }
-                    if (lane == 0 || lane == 31) {
-                        const int b = lane == 0 ? 0 : 2;
-                        const int xx = lane == 0 ? max(xc - 1, 0) : min(xc + 1, w2 - 1);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const int yy = min(max(gy + a - 1, 0), h2 - 1);
-#pragma unroll
-                            for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(fm + ((size_t)yy * w2 + xx) * 5 + k);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            int yy = min(max(gy + a - 1, 0), h2 - 1), xx = min(max(gx + b - 1, 0), w2 - 1);
-                            const float *src = fm + ((size_t)yy * w2 + xx) * 5;
-#pragma unroll
-                            for (int k = 0; k < 5; ++k) nb[a][b][k] = __ldg(src + k);
-                        }
-                }
+                resid_nb(p, n, gy, gx, lane, p.tw_log >= 5, nb);
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
                 ptx::tc_fence_after();
 #pragma unroll
@@ -689,18 +840,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ptx::tmem_ld16(tbase + c, r);
                     ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = c + j, pj = col / 5, co = col % 5, py = pj >> 1, px = pj & 1;
-                        if (col < 20 && valid) {
-                            const float ly = py ? 0.25f : 0.75f, lx = px ? 0.25f : 0.75f;
-                            float up = (1.f - ly) * ((1.f - lx) * nb[py][px][co] + lx * nb[py][px + 1][co]) +
-                                       ly * ((1.f - lx) * nb[py + 1][px][co] + lx * nb[py + 1][px + 1][co]);
-                            const float sc = p.acc_scale ? __ldg(p.acc_scale + co) : 1.f;
-                            float x = __uint_as_float(r[j]) * sc + __ldg(p.bias + co) + up * (co < 4 ? 2.f : 1.f);
-                            size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
-                            ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = x;
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        if (c + j < 20 && valid) resid_store(p, nb, n, gy, gx, c + j, __uint_as_float(r[j]));
                 }
             } else {
             if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
@@ -1085,6 +1226,43 @@ int launch_halo_grp(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensor
     return FVV_OK;
 }
 
+// Folded column taps, NCK channel blocks: a stage is the 128 rows of four 32-pixel
+// boxes, the 3 x NCK folded weight slices stay resident.  At least 3 stages per CTA.
+template <int BN, int CK, int F8, int NCK> struct KxfCfg {
+    static constexpr uint32_t ES = F8 ? 1 : 2;
+    static constexpr uint32_t A = (128 * CK * ES + 1023) & ~1023u;
+    static constexpr uint32_t BR = (3 * NCK * BN * CK * ES + 1023) & ~1023u;
+    static constexpr uint32_t KST = 4 * 2 * 300 * 4; // Eq. 2 output staging, 4 epilogue warps
+    static constexpr int stages_for(int ctas) { return (int)((kSmemBudget / ctas - 2048 - BR - KST) / A); }
+    static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 3 ? ctas_for(c - 1) : c; }
+    static constexpr int CTAS = ctas_for(3);
+    static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
+    static constexpr size_t SMEM = (size_t)STAGES * A + BR + KST + sizeof(Bars) + 1024;
+    static_assert(STAGES >= 2 && STAGES < 16 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "folded-tap config");
+};
+
+template <int BN, int CK, int F8, int NCK>
+int launch_kxf(const CUtensorMap &ma, const CUtensorMap &mk, const TcParams &p, cudaStream_t st) {
+    using C = KxfCfg<BN, CK, F8, NCK>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, 0, 0, 2, 0, NCK>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_set = true;
+    }
+    if (!g_num_sms) {
+        int dev;
+        FVV_CHECK_CUDA(cudaGetDevice(&dev));
+        FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int slots = g_num_sms * C::CTAS;
+    int grid = p.num_tiles < slots ? p.num_tiles : slots;
+    kern<<<grid, kThreads, C::SMEM, st>>>(ma, mk, ma, p);
+    count_launch();
+    FVV_CHECK_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
 template <int BN, int F8, int TS, int MC, int MT = 1>
 int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                 cudaStream_t st) {
@@ -1249,6 +1427,40 @@ int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &
 // x 4 taps for the transposed conv) and build its B tensor map.
 int tc_prepare_fp8(fvv_interp *h, const float *blob);
 
+// Layers whose column taps are folded into N: the VIB t1 transposed convs (all four
+// phases, 4 x 5 columns per tap: N = 64 instead of 3 MMAs of N = 32 per K step).
+bool tc_kxf_layer(int li) {
+    const LayerDef &L = kLayers[li];
+    return L.kind == K_CONVT && tc_all_phases(li) && L.co == 5;
+}
+
+// Folded weights from the per-tap packing pk ([9][cop][cip], element type T): slice ky
+// holds rows kx * G + j = row j of tap (ky, kx), padded to nk rows; uploaded to tw.wk
+// with map_k (box: one channel block of the 3 slices).
+template <typename T>
+int fold_column_taps(fvv_interp *h, TcWeights &tw, const std::vector<T> &pk, int cop, int cip, int G, int ck) {
+    const int nk = pad16(3 * G);
+    std::vector<T> f((size_t)3 * nk * cip);
+    memset(f.data(), 0, f.size() * sizeof(T)); // +0 in bf16 and in E4M3
+    for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx)
+            for (int j = 0; j < G; ++j)
+                memcpy(&f[((size_t)ky * nk + kx * G + j) * cip], &pk[((size_t)(ky * 3 + kx) * cop + j) * cip],
+                       cip * sizeof(T));
+    FVV_TRY(dalloc(h, &tw.wk, f.size() * sizeof(T)));
+    FVV_CHECK_CUDA(cudaMemcpy(tw.wk, f.data(), f.size() * sizeof(T), cudaMemcpyHostToDevice));
+    const cuuint64_t es = sizeof(T);
+    cuuint64_t dims[3] = {(cuuint64_t)cip, (cuuint64_t)nk, 3};
+    cuuint64_t strides[2] = {(cuuint64_t)cip * es, (cuuint64_t)nk * cip * es};
+    cuuint32_t box[3] = {(cuuint32_t)ck, (cuuint32_t)nk, 3};
+    g_encode_u8 = sizeof(T) == 1;
+    int rc = encode((CUtensorMap *)tw.map_k, 3, tw.wk, dims, strides, box, ck * (int)es);
+    g_encode_u8 = false;
+    FVV_TRY(rc);
+    tw.kxf_n = nk;
+    return FVV_OK;
+}
+
 int tc_prepare(fvv_interp *h, const float *blob) {
     FVV_TRY(get_encoder());
     if (h->o.pad_mode != FVV_PAD_ZERO) {
@@ -1256,6 +1468,8 @@ int tc_prepare(fvv_interp *h, const float *blob) {
         return FVV_EINVAL;
     }
     size_t off = 0;
+    struct Fold { int li; std::vector<bf16> pk; int cop, cip, G, ck; };
+    std::vector<Fold> folds;
     for (int i = 0; i < kNumLayers; ++i) {
         const LayerDef &L = kLayers[i];
         const bool t3 = tc_all_phases(i);
@@ -1319,7 +1533,13 @@ int tc_prepare(fvv_interp *h, const float *blob) {
             box[1] = (cuuint32_t)(cop / 2);
             FVV_TRY(encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, ck * 2));
         }
+        if (tc_kxf_layer(i)) folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
     }
+    // folded copies allocated after every layer's own weights: the per-layer weight
+    // allocations keep the addresses they have without them (the per-tap convs reload
+    // their slices from L2 on every tile, and where those land in L2 was measured to
+    // change their speed by up to 40 %)
+    for (Fold &f : folds) FVV_TRY(fold_column_taps(h, h->tc[f.li], f.pk, f.cop, f.cip, f.G, f.ck));
     if (h->o.precision == FVV_FP8) FVV_TRY(tc_prepare_fp8(h, blob));
     return FVV_OK;
 }
@@ -1329,6 +1549,8 @@ int tc_prepare(fvv_interp *h, const float *blob) {
 // (9 conv taps, or the transposed conv's 16 phase x tap slices in the BF16 order).
 int tc_prepare_fp8(fvv_interp *h, const float *blob) {
     size_t off = 0;
+    struct Fold8 { int li; std::vector<uint8_t> pk; int rows, cip, G; };
+    std::vector<Fold8> folds8;
     for (int i = 0; i < kNumLayers; ++i) {
         const LayerDef &L = kLayers[i];
         const float *w = blob + off;
@@ -1397,7 +1619,9 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, 128);
         g_encode_u8 = false;
         FVV_TRY(rc);
+        if (tc_kxf_layer(i)) folds8.push_back({i, std::move(pk), rows, L.ci, t3 ? 4 * L.co : L.co});
     }
+    for (Fold8 &f : folds8) FVV_TRY(fold_column_taps(h, h->tc8[f.li], f.pk, f.rows, f.cip, f.G, 128));
     FVV_TRY(dalloc(h, (void **)&h->d_amax, kNumLayers * sizeof(float)));
     FVV_CHECK_CUDA(cudaMemset(h->d_amax, 0, kNumLayers * sizeof(float)));
     return FVV_OK;
@@ -1442,12 +1666,19 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     // output pixels, one box of 129 pixel pairs per row tap, resident weights
     const bool s2h = force < 0 && p.mode == MODE_S2 && !f8 && cip == ck && in_cs == cip && in_coff == 0 &&
                      s2h_ok(bn, ck) && p.gw >= 96 && (!epi || epi->mode == EPI_STORE);
+    // column taps folded into N (VIB t1): rows of 120 output pixels
+    // (the epilogue reads the accumulator in 4-column loads: 4 C_out % 4 == 0)
+    // (grids narrower than 256: the per-tap-box path, measured faster on VIB0's 240-wide grid)
+    const bool kxf = halo && tc_kxf_layer(li) && tw.kxf_n == 64 && p.mode == MODE_T3 && cip == 128 && L.co == 5 &&
+                     p.gw >= 256 &&
+                     (!epi || epi->mode == EPI_STORE || epi->mode == EPI_RESID);
     const int halo_mt = bn == 256 ? kHaloMT256 : 1;
     if (halo) s = Shape{halo_mt - 1, 7};
     if (s2h) s = Shape{0, 7};
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
-    p.tiles_x = ceil_div(p.gw, 1 << s.tw_log);
+    p.tiles_x = kxf ? ceil_div(p.gw, kKxfTile) : ceil_div(p.gw, 1 << s.tw_log);
+    p.kxf = kxf ? 1 : 0;
     long long tiles = (long long)N * p.tiles_y * p.tiles_x * (p.mode == MODE_T ? 4 : 1);
     if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
     p.num_tiles = (int)tiles;
@@ -1468,7 +1699,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them
         bool ok = (epi->mode == EPI_STORE) ||
-                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5) ||
+                  (epi->mode == EPI_RESID && p.mode == MODE_T3 && L.co == 5 && bn == 32 && out_f32 && out_cs == 5 &&
+                   out_coff == 0) ||
                   (epi->mode == EPI_OUTPUT && p.mode == MODE_S1 && L.co == 3 && bn == 16 && !f8 && epi->ib &&
                    epi->final_out_ref && epi->crop_h <= p.gh && epi->crop_w <= p.gw);
         if (!ok) { set_error("layer %s: unsupported fused epilogue", L.name); return FVV_EINVAL; }
@@ -1494,8 +1726,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
-        // halo boxes: MT rows x 130 pixels
-        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(halo ? tw_ + 2 : tw_), (cuuint32_t)th_, 1};
+        // halo boxes: MT rows x 130 pixels (folded column taps: 32 pixels, four per stage)
+        cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(kxf ? 32 : (halo ? tw_ + 2 : tw_)), (cuuint32_t)th_, 1};
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);
     }
     g_encode_u8 = false;
@@ -1509,7 +1741,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         // than with the staging buffers)
         const int oes = p.out_fp8 ? 1 : 2;
         const int chb = p.mode == MODE_T3 ? L.co * oes : (bn * oes < 128 ? bn * oes : 128);
-        p.tma_store = (!epi || epi->mode == EPI_STORE) && !out_f32 &&
+        p.tma_store = !kxf && (!epi || epi->mode == EPI_STORE) && !out_f32 &&
                       (p.mode == MODE_T3 ? 4 * L.co == bn && bn == 128 && L.co % 32 == 0 : L.co == bn) &&
                       (chb == 32 || chb == 64 || chb == 128) && (out_cs * oes) % 16 == 0 &&
                       (out_coff * oes) % 16 == 0 && ((uintptr_t)out % 16) == 0;
@@ -1535,6 +1767,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             FVV_TRY(rc);
         }
     }
+    if (kxf)
+        return f8 ? launch_kxf<64, 128, 1, 1>(ma, *(const CUtensorMap *)tw.map_k, p, st)
+                  : launch_kxf<64, 64, 0, 2>(ma, *(const CUtensorMap *)tw.map_k, p, st);
     if (s2h)
         return p.tma_store ? dispatch_s2h_ts<1>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st)
                            : dispatch_s2h_ts<0>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st);

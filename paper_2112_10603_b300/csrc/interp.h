@@ -37,6 +37,11 @@ struct TcWeights {
     alignas(64) unsigned char map[128] = {}; // host CUtensorMap of w (B operand)
     alignas(64) unsigned char map_half[128] = {}; // same, box of C_out / 2 rows (cluster-pair loads)
     alignas(64) unsigned char map3[128] = {};     // same, box of 3 consecutive taps (grouped halo stages)
+    // folded column taps: per row tap ky one slice of kxf_n rows (kx * G + j, G = output
+    // columns per tap), [3][kxf_n][Ci_pad]; map_k boxes the 3 row taps of one channel block
+    void *wk = nullptr;
+    alignas(64) unsigned char map_k[128] = {};
+    int kxf_n = 0;
     int ci_pad = 0, co_pad = 0;
 };
 
@@ -117,6 +122,7 @@ int tc_prepare(fvv_interp *h, const float *blob);
 int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
             void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
+bool tc_kxf_layer(int layer);   // column taps folded into N (tiles of 120 pixels)
 // FP8 layers: every VIBlock conv with 128 or 256 input channels -- c1 (128 -> 256,
 // stride 2), the six 256 -> 256 convs m0-m5, t0 (256 -> 128 transposed) and t1 (128 -> 5
 // transposed, all phases); their producers are the layer before (c0 .. t0) and write

@@ -15,11 +15,17 @@ column taps read it 0, 1, 2 rows in.  Checks:
 * the whole BF16 forward with the halo tiles equals, bit for bit, the same
   forward with every layer forced onto plain 1 x 128 tiles: both accumulate
   the K loop in the order (row tap, channel block, column tap), or (channel block,
-  tap) for the per-phase transposed convs.
+  tap) for the per-phase transposed convs (the VIB t1 convs, whose column taps are
+  folded into N and summed after the K loop, run on plain tiles in both);
+* the forward with t1's folded column taps matches the one with t1 on plain tiles to
+  FP32 rounding of that sum (stage flows, Eq. 2, and the views).
 
 The transposed convs with C_out <= 32 (VIB t1, RefineNet d2, d3) run as one 3x3 conv
 over all four output phases (N = 4 C_out); d2's phases are stored by TMA through the
-pixel-pair map, one phase per staged chunk.
+pixel-pair map, one phase per staged chunk.  VIB t1 folds its three column taps into N
+(N = 3 x 20 -> 64) on grids at least 256 wide: rows of 120 output pixels, four 32-pixel
+boxes per (row tap, channel block); the layer tests run it on a grid 370 (= 3 x 120 + 10)
+wide, and vib2.t1 on 131 keeps the per-row-tap boxes.
 """
 import json
 
@@ -37,7 +43,7 @@ pytestmark = pytest.mark.gpu
 # N = 16 tile with 3 real columns) and the all-phase transposed convs (t1, d3, and d2
 # with TMA-stored phases)
 HALO_LAYERS = ["vib2.m0", "vib0.m5", "vib2.t1", "ctx.c7", "ref.e1b", "ref.e3b", "ref.d3", "ctx.c1", "ctx.c3",
-               "ref.e0b", "ref.d2", "ref.out"]
+               "ref.e0b", "ref.d2", "ref.out", "vib1.t1"]
 
 
 @pytest.fixture(scope="module")
@@ -61,8 +67,9 @@ def test_halo_layer_matches_oracle(torch_cuda, name):
     _, kind, ci, co, stride, relu = weights.manifest()[li]
     assert stride == 1 or kind == "convT"
     rng = np.random.default_rng(300 + li)
-    # grid widths 260 = 2 x 128 + 4 (conv) and 131 = 128 + 3 (transposed conv input)
-    H, W = (3, 131) if kind == "convT" else (3, 260)
+    # grid widths 260 = 2 x 128 + 4 (conv) and 131 = 128 + 3 (transposed conv input);
+    # vib1.t1: 370 = 3 x 120 + 10 (four tiles of the folded column taps, grids >= 256)
+    H, W = ((3, 370) if name == "vib1.t1" else (3, 131)) if kind == "convT" else (3, 260)
     # one image of vib2.m0: 3 x 3 = 9 tiles, an odd count for the 256-channel layers'
     # cluster pairs (the last pair's second tile is a filler that must not be stored)
     n = 1 if name == "vib2.m0" else 2
@@ -168,12 +175,41 @@ def test_halo_network_bitwise_plain_tiles(torch_cuda, tmp_path):
     L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
     ts = [0.3, 0.8]
     it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=2)
+    key = f"{H}x{W} n2 p{fvv.FVV_BF16}"
+    # t1 (folded column taps) on plain tiles, every other layer on its default tiles
+    t1_plain = tmp_path / "t1.json"
+    t1_plain.write_text(json.dumps({key: {f"vib{s}.t1": 7 for s in range(3)}}))
+    it.autotune(2, str(t1_plain))
     halo = it.run(L, R, ts).cpu().numpy()
     # force every layer onto plain tiles 128 pixels wide through a tile cache entry
     cache = tmp_path / "plain.json"
-    key = f"{H}x{W} n2 p{fvv.FVV_BF16}"
     cache.write_text(json.dumps({key: {m[0]: 7 for m in weights.manifest()}}))
     it.autotune(2, str(cache))
     plain = it.run(L, R, ts).cpu().numpy()
     fvv.fvv_interp_status(it.h)
     np.testing.assert_array_equal(halo, plain)
+
+
+def test_folded_t1_network_matches_plain_t1(torch_cuda, tmp_path):
+    """VIB t1 with its column taps folded into N against t1 on plain tiles, the rest of
+    the network unchanged: the two differ only in the FP32 order of the three column
+    taps' sums, so the stage flows (Eq. 2 fused into t1) agree to far below a pixel and
+    the views to BF16 noise."""
+    torch = torch_cuda
+    H, W = 64, 512
+    left, right = pair(23, H, W, 10.0)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.4, 0.7]
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=2)
+    folded = it.run(L, R, ts).cpu().numpy()
+    flows = [it.peek(f"vib{s}").copy() for s in range(3)]
+    cache = tmp_path / "t1.json"
+    cache.write_text(json.dumps({f"{H}x{W} n2 p{fvv.FVV_BF16}": {f"vib{s}.t1": 7 for s in range(3)}}))
+    it.autotune(2, str(cache))
+    plain = it.run(L, R, ts).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    for s in range(3):
+        d = np.abs(it.peek(f"vib{s}") - flows[s])
+        assert d.max() < 0.05, (s, float(d.max()))
+    d = np.abs(folded - plain)
+    assert d.max() < 0.05 and d.mean() < 1e-3, (float(d.max()), float(d.mean()))
