@@ -1428,7 +1428,7 @@ int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &
 int tc_prepare_fp8(fvv_interp *h, const float *blob);
 
 // Layers whose column taps are folded into N: the VIB t1 transposed convs (all four
-// phases, 4 x 5 columns per tap: N = 64 instead of 3 MMAs of N = 32 per K step).
+// phases, 4 x 5 columns per tap: N = 64 instead of 3 MMAs of N = 32 per K step), BF16.
 bool tc_kxf_layer(int li) {
     const LayerDef &L = kLayers[li];
     return L.kind == K_CONVT && tc_all_phases(li) && L.co == 5;
@@ -1549,8 +1549,6 @@ int tc_prepare(fvv_interp *h, const float *blob) {
 // (9 conv taps, or the transposed conv's 16 phase x tap slices in the BF16 order).
 int tc_prepare_fp8(fvv_interp *h, const float *blob) {
     size_t off = 0;
-    struct Fold8 { int li; std::vector<uint8_t> pk; int rows, cip, G; };
-    std::vector<Fold8> folds8;
     for (int i = 0; i < kNumLayers; ++i) {
         const LayerDef &L = kLayers[i];
         const float *w = blob + off;
@@ -1619,9 +1617,7 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, 128);
         g_encode_u8 = false;
         FVV_TRY(rc);
-        if (tc_kxf_layer(i)) folds8.push_back({i, std::move(pk), rows, L.ci, t3 ? 4 * L.co : L.co});
     }
-    for (Fold8 &f : folds8) FVV_TRY(fold_column_taps(h, h->tc8[f.li], f.pk, f.rows, f.cip, f.G, 128));
     FVV_TRY(dalloc(h, (void **)&h->d_amax, kNumLayers * sizeof(float)));
     FVV_CHECK_CUDA(cudaMemset(h->d_amax, 0, kNumLayers * sizeof(float)));
     return FVV_OK;
@@ -1668,8 +1664,10 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
                      s2h_ok(bn, ck) && p.gw >= 96 && (!epi || epi->mode == EPI_STORE);
     // column taps folded into N (VIB t1): rows of 120 output pixels
     // (the epilogue reads the accumulator in 4-column loads: 4 C_out % 4 == 0)
-    // (grids narrower than 256: the per-tap-box path, measured faster on VIB0's 240-wide grid)
-    const bool kxf = halo && tc_kxf_layer(li) && tw.kxf_n == 64 && p.mode == MODE_T3 && cip == 128 && L.co == 5 &&
+    // (grids narrower than 256 keep the per-row-tap boxes, measured faster on VIB0's
+    // 240-wide grid; so does E4M3, whose K = 32 MMAs already take a third as many steps:
+    // VIB2 t1 262 us there against 413 folded)
+    const bool kxf = !f8 && halo && tc_kxf_layer(li) && tw.kxf_n == 64 && p.mode == MODE_T3 && cip == 128 && L.co == 5 &&
                      p.gw >= 256 &&
                      (!epi || epi->mode == EPI_STORE || epi->mode == EPI_RESID);
     const int halo_mt = bn == 256 ? kHaloMT256 : 1;
@@ -1768,8 +1766,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         }
     }
     if (kxf)
-        return f8 ? launch_kxf<64, 128, 1, 1>(ma, *(const CUtensorMap *)tw.map_k, p, st)
-                  : launch_kxf<64, 64, 0, 2>(ma, *(const CUtensorMap *)tw.map_k, p, st);
+        return launch_kxf<64, 64, 0, 2>(ma, *(const CUtensorMap *)tw.map_k, p, st);
     if (s2h)
         return p.tma_store ? dispatch_s2h_ts<1>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st)
                            : dispatch_s2h_ts<0>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st);

@@ -96,7 +96,7 @@ def test_fp8_strided_and_transposed_layers(torch_cuda, name):
     sw = s_w[:, None, None, None] if kind == "conv" else s_w[None, :, None, None]
     wq_codes, wq = _e4m3(torch, w / sw)
     rng = np.random.default_rng(li)
-    # vib2.t1 on 370 = 3 x 120 + 10: the folded column taps (grids >= 256 wide)
+    # vib2.t1 also on a wider grid, 370 = 2 x 128 + 114
     n, h, ww = 2, (6 if kind == "conv" else 3), (260 if kind == "conv" else (370 if name == "vib2.t1" else 131))
     x = np.maximum(rng.standard_normal((n, h, ww, ci)), 0) * (100 * s_a)
     xq_codes, xq = _e4m3(torch, x / s_a)
