@@ -67,6 +67,7 @@ struct TcParams {
     float *amax;            // calibration: running max |output| (NULL: off)
     int tma_store;          // epilogue stages each warp's 32 rows in shared memory, TMA stores them
     int kxf;                // column taps folded into N: tiles of kKxfTile output pixels of one row
+    int wcopies;            // per-tap stride-2 path: weight copies (CTA b reads copy b % wcopies)
 };
 
 // Column taps folded into N (3x3 stride-1 convs and the all-phase transposed convs with
@@ -503,7 +504,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         int half = kx == 1 ? 0 : 1, rpar = ky == 1 ? 0 : 1;
                         ptx::tma_load_5d(da, &tmA, fb, half * p.in_cs + p.in_coff + c0, x0 - (kx == 0 ? 1 : 0), rpar,
                                          y0 - (ky == 0 ? 1 : 0), n);
-                        ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
+                        ptx::tma_load_3d(db, &tmB, fb, c0, 0,
+                                         tap + (p.wcopies > 1 ? 9 * (int)(blockIdx.x % (unsigned)p.wcopies) : 0));
                     } else {
                         // K order (channel block, tap)
                         tap = kb & 3;
@@ -1542,6 +1544,22 @@ int tc_prepare(fvv_interp *h, const float *blob) {
     // their slices from L2 on every tile, and where those land in L2 was measured to
     // change their speed by up to 40 %)
     for (Fold &f : folds) FVV_TRY(fold_column_taps(h, h->tc[f.li], f.pk, f.cop, f.cip, f.G, f.ck));
+    // the VIB1 / VIB2 input convs (18 -> 128, stride 2, per-tap tiles): four weight copies
+    for (int i = 0; i < kNumLayers; ++i) {
+        const LayerDef &L = kLayers[i];
+        if (!(L.kind == K_CONV && L.stride == 2 && L.ci == 18 && L.co == 128)) continue;
+        TcWeights &tw = h->tc[i];
+        const int copies = 4, cip = tw.ci_pad, cop = tw.co_pad, ck = ck_of(cip);
+        const size_t one = (size_t)9 * cop * cip * 2;
+        FVV_TRY(dalloc(h, &tw.wrep, copies * one));
+        for (int c = 0; c < copies; ++c)
+            FVV_CHECK_CUDA(cudaMemcpy((char *)tw.wrep + c * one, tw.w, one, cudaMemcpyDeviceToDevice));
+        cuuint64_t dims[3] = {(cuuint64_t)cip, (cuuint64_t)cop, (cuuint64_t)(9 * copies)};
+        cuuint64_t strides[2] = {(cuuint64_t)cip * 2, (cuuint64_t)cip * cop * 2};
+        cuuint32_t box[3] = {(cuuint32_t)ck, (cuuint32_t)cop, 1};
+        FVV_TRY(encode((CUtensorMap *)tw.map_rep, 3, tw.wrep, dims, strides, box, ck * 2));
+        tw.wcopies = copies;
+    }
     if (h->o.precision == FVV_FP8) FVV_TRY(tc_prepare_fp8(h, blob));
     return FVV_OK;
 }
@@ -1775,6 +1793,10 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     if (halo)
         return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half,
                              *(const CUtensorMap *)tw.map3, mc, p, st);
+    if (p.mode == MODE_S2 && !f8 && tw.wcopies > 1) {
+        p.wcopies = tw.wcopies;
+        return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map_rep, mc, p, st);
+    }
     return dispatch(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, mc, p, st);
 }
 

@@ -42,6 +42,11 @@ struct TcWeights {
     void *wk = nullptr;
     alignas(64) unsigned char map_k[128] = {};
     int kxf_n = 0;
+    // per-tap stride-2 input convs: wcopies copies of w side by side ([copies][taps]...),
+    // CTAs read copy blockIdx % wcopies (spreads the hot weight lines over more of L2)
+    void *wrep = nullptr;
+    alignas(64) unsigned char map_rep[128] = {};
+    int wcopies = 1;
     int ci_pad = 0, co_pad = 0;
 };
 
