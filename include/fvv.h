@@ -168,8 +168,12 @@ int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in
  * a layer with more weights is rejected with FVV_ESHAPE.  All calls share that
  * array and it keeps the last call's contents, so calls that overlap on the GPU
  * (different streams, or another thread) race: serialise them.  The first call on
- * a device looks up the array's device address (with that device current); make
- * that first call before any stream capture.  Asynchronous on `stream`. */
+ * a device loads this entry point's module, which is when the driver creates the
+ * array on that device (that step may synchronise the device), and looks up the
+ * array's device address (with that device current).  So make one warm-up call per
+ * device at initialisation, before any stream capture and outside any real-time
+ * loop; calls after it allocate nothing.  `stream` must belong to the current
+ * device (FVV_EINVAL otherwise).  Asynchronous on `stream`. */
 int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in, int in_cs, int in_coff, int n,
                       int H, int W, float *out, int out_cs, int out_coff, void *stream);
 
@@ -195,6 +199,19 @@ int fvv_stitch_cluster(const float *center, const float *const *side_views, int 
  * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */
 int fvv_interp_status(fvv_interp *h);
+
+/* Fault injection for tests of the failure detection (the paper has no counterpart;
+ * its system claims elasticity without a mechanism, Sec. 3.2).  Arms the NEXT
+ * fvv_interp_layer call on this handle: in its tensor-core kernel the MMA warp first
+ * waits on a shared-memory barrier that nothing signals, for at most `cycles` SM
+ * clock cycles.  The wait runs out, the kernel records code 6 in the handle's error
+ * word, the other warp roles stop, the copies already issued land, TMEM is freed and
+ * the kernel returns without writing its output; fvv_interp_status then returns
+ * FVV_ETIMEOUT and clears the word.  No GPU fault is involved and the context stays
+ * usable.  The knob is never live inside fvv_interp_run (so no captured graph holds
+ * it) and has no effect on the FP32 path, whose kernels have no waits.
+ * cycles in [1000, 2^31], else FVV_EINVAL. */
+int fvv_interp_inject_stall(fvv_interp *h, long long cycles);
 
 /* FP8 calibration (FVV_FP8 handles only; required before their first run).
  * On FP8 handles every VIBlock conv with 128 or 256 input channels -- c1, the six

@@ -64,6 +64,7 @@ def lib():
         L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
         L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
         L.fvv_interp_status.argtypes = [_P]
+        L.fvv_interp_inject_stall.argtypes = [_P, ctypes.c_longlong]
         L.fvv_interp_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_char_p]
         L.fvv_layer_noalloc.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
@@ -220,6 +221,11 @@ def fvv_interp_autotune(h: int, n_views: int, cache_path: str | None = None):
 
 def fvv_interp_status(h: int):
     _check(lib().fvv_interp_status(h))
+
+
+def fvv_interp_inject_stall(h: int, cycles: int):
+    """Arm the next fvv_interp_layer call's bounded-wait fault injection (see fvv.h)."""
+    _check(lib().fvv_interp_inject_stall(h, cycles))
 
 
 def fvv_interp_profile(h: int, enable: bool):

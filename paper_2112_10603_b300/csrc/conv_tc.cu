@@ -15,8 +15,8 @@
 //     input grid (phase p: taps read rows q - t (p=0) or q + 1 - t (p=1)); with few
 //     output channels all 4 phases at once as one 3x3 conv (MODE_T3, N = 4 C_out);
 //   * E4M3 operands (kind::f8f6f4, K = 32 per MMA) for the FP8 layers.
-// Halo tiles, grouped stages, cluster pairs, the stride-2 pair halo and the TMA-store
-// epilogue are described at the kernel template below.
+// Halo tiles, grouped stages, the stride-2 pair halo and the TMA-store epilogue are
+// described at the kernel template below.
 // Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer (+ TMEM owner),
 // warps 2-5 = epilogue (TMEM -> registers -> bias, ReLU, BF16/FP32 -> global).
 // The accumulator is double-buffered in TMEM so the epilogue of one tile runs
@@ -68,6 +68,8 @@ struct TcParams {
     int tma_store;          // epilogue stages each warp's 32 rows in shared memory, TMA stores them
     int kxf;                // column taps folded into N: tiles of kKxfTile output pixels of one row
     int wcopies;            // per-tap stride-2 path: weight copies (CTA b reads copy b % wcopies)
+    long long stall_cycles; // fault injection (tests): > 0 makes the MMA warp wait on a barrier
+                            // nothing signals, for at most this many cycles, then abort
 };
 
 // Column taps folded into N (3x3 stride-1 convs and the all-phase transposed convs with
@@ -87,11 +89,13 @@ __device__ __forceinline__ uint8_t to_e4m3(float v) {
 
 struct __align__(8) Bars {
     uint64_t full[16], empty[16], tmem_full[2], tmem_empty[2], drain;
+    uint64_t never; // signalled by nothing: the fault-injection wait
     uint32_t tmem_base;
     int abort;
 };
 
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort, int *err, int code) {
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort, int *err, int code,
+                                         long long limit = kWaitCycles) {
     long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (ptx::mbar_try_wait(bar, parity)) return true;
@@ -99,7 +103,7 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
             if (*abort) return false;
             long long now = clock64();
             if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitCycles) {
+            else if (now - t0 > limit) {
                 *abort = 1;
                 atomicExch(err, code);
                 return false;
@@ -229,11 +233,6 @@ template <int BN, int MT> struct AccCfg {
 // (STAGES ring) and B slices (STAGES_B ring) are pipelined separately.  K order is
 // (ky, block, kx) on both paths.  With MT = 2 each weight slice feeds two MMAs.
 // TS = 1: shared-memory staging for the TMA-store epilogue (used when p.tma_store).
-// MC = 1 (halo only): clusters of 2 CTAs on neighbouring tiles share every weight
-// slice: each CTA loads one half of its N rows and multicasts it into both CTAs'
-// rings, halving the weight traffic from L2.  A slot of the B ring is released by
-// both CTAs' MMA commits; tiles go in pairs (a pair's odd last member is computed
-// on a clamped tile and not stored).
 // GRP = 2: the same with the nine weight slices of a one-block layer resident in shared
 // memory (loaded once per CTA); a stage is the A box alone.
 // GRP = 1 (halo, small N): one stage holds a (row tap, channel block)'s A box AND its
@@ -249,7 +248,7 @@ template <int BN, int MT> struct AccCfg {
 // resident-weight grouped path (GRP = 2): a stage is the four 32-pixel boxes of one
 // (row tap, channel block), the weights are 3 x KXF folded slices of N rows.
 template <int BN, int CK, int MT, int STAGES, int CTAS, int F8, int HALO = 0, int STAGES_B = STAGES, int TS = 0,
-          int MC = 0, int GRP = 0, int S2H = 0, int KXF = 0>
+          int GRP = 0, int S2H = 0, int KXF = 0>
 __global__ void __launch_bounds__(kThreads, CTAS)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, const TcParams p) {
@@ -262,10 +261,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int NB = 3;     // weight slices (column taps) per halo box
     constexpr uint32_t A_STRIDE = (A_BYTES + 1023) & ~1023u, B_STRIDE = (B_BYTES + 1023) & ~1023u;
     static_assert(!HALO || STAGES + STAGES_B <= 16, "halo config");
-    static_assert(!MC || (HALO && ROW_BYTES == 128), "weight multicast runs on the 128-byte halo path");
     // (BN % 8 == 0: each weight slice of a grouped box starts on a swizzle-pattern boundary)
-    static_assert(!GRP || (HALO && !MC && BN % 8 == 0), "grouped stages run on the halo path");
-    static_assert(!S2H || (!HALO && !MC && !GRP && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
+    static_assert(!GRP || (HALO && BN % 8 == 0), "grouped stages run on the halo path");
+    static_assert(!S2H || (!HALO && !GRP && MT == 1 && !F8 && STAGES < 16 && BN % 8 == 0 &&
                            (ROW_BYTES == 32 || ROW_BYTES == 64)),
                   "stride-2 pair halo: one 16/32-channel block, pair rows of 64/128 bytes");
     static_assert(!KXF || (GRP == 2 && MT == 1 && !TS && KXF <= 2), "folded column taps: resident grouped stages");
@@ -301,13 +299,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // S2H: full[STAGES] = the resident weights
         for (int s = 0; s < (HALO && !GRP ? STAGES + STAGES_B : STAGES + (S2H || GRP == 2 ? 1 : 0)); ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), MC && s >= STAGES ? 2 : 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(ptx::smem_u32(&bars->tmem_full[a]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->tmem_empty[a]), 128);
         }
         ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
+        ptx::mbar_init(ptx::smem_u32(&bars->never), 1);
         bars->abort = 0;
         ptx::fence_barrier_init();
         ptx::fence_proxy_async_smem();
@@ -322,12 +321,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (MC) ptx::cluster_sync(); // the peer's barriers are initialised before any multicast
     const uint32_t tmem = bars->tmem_base;
     const int kblocks = p.taps * p.nck;
-    const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
-    // with MC, both CTAs of a cluster walk the same number of tile pairs
-    const int t_end = MC ? ((p.num_tiles + 1) & ~1) : p.num_tiles;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -426,9 +421,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t pa = 0, pb = 0;
             long long issued_a = 0, issued_b = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < t_end && !*abort && !stop; t += gridDim.x) {
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t < p.num_tiles ? t : p.num_tiles - 1, ph, n, y0, x0);
+                tile_coords(p, t, ph, n, y0, x0);
                 // boxes in K order (ky, channel block)
                 const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && !stop; ++grp) {
@@ -444,23 +439,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             const int slot = STAGES + sb;
                             if (!wait_bar(ptx::smem_u32(&bars->empty[slot]), pb ^ 1, abort, p.err, 1)) { stop = true; break; }
                             uint32_t fbb = ptx::smem_u32(&bars->full[slot]);
-                            ptx::mbar_arrive_expect_tx(fbb, B_BYTES); // both halves land here
-                            if (MC)
-                                ptx::tma_load_3d_mc(ptx::smem_u32(sB + sb * B_STRIDE) + rank * (B_BYTES / 2), &tmB, fbb,
-                                                    c * CK, (int)rank * (BN / 2), ky * 3 + kx, (uint16_t)3);
-                            else
-                                ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
+                            ptx::mbar_arrive_expect_tx(fbb, B_BYTES);
+                            ptx::tma_load_3d(ptx::smem_u32(sB + sb * B_STRIDE), &tmB, fbb, c * CK, 0, ky * 3 + kx);
                             ++issued_b;
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
-                }
-            }
-            if (MC && !*abort && !stop) {
-                // every B slot's last use released by both CTAs: no commit of either
-                // MMA warp is still on its way to the other CTA's barriers
-                for (int i = 0; i < STAGES_B; ++i) {
-                    if (!wait_bar(ptx::smem_u32(&bars->empty[STAGES + sb]), pb ^ 1, abort, p.err, 5)) break;
-                    if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                 }
             }
             if (*abort || stop) {
@@ -533,6 +516,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
+        // fault injection: a wait that runs out (nothing arrives on `never`) records
+        // code 6 and raises the abort flag before any MMA is issued; the producer then
+        // stops and lets its copies land, the epilogue warps leave, TMEM is freed
+        if (lane == 0 && p.stall_cycles > 0)
+            wait_bar(ptx::smem_u32(&bars->never), 0, abort, p.err, 6, p.stall_cycles);
         if (lane == 0 && S2H) {
             int s = 0;
             uint32_t ph_bit = 0;
@@ -643,7 +631,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem + acc * (MT * BN);
@@ -674,8 +662,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             }
                             accumulate = 1;
                             issued_any = true;
-                            if (MC) ptx::mma_commit_mc(ptx::smem_u32(&bars->empty[STAGES + sb]), (uint16_t)3);
-                            else ptx::mma_commit(ptx::smem_u32(&bars->empty[STAGES + sb]));
+                            ptx::mma_commit(ptx::smem_u32(&bars->empty[STAGES + sb]));
                             if (++sb == STAGES_B) { sb = 0; pb ^= 1; }
                         }
                         if (!ok) break;
@@ -750,12 +737,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         // fused network output (N = 16 tiles): the cropped output buffer
         float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
-        for (int t = blockIdx.x; t < t_end && !*abort; t += gridDim.x) {
+        for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
-            const bool phantom = t >= p.num_tiles; // pair filler: computed, never stored
-            tile_coords(p, phantom ? p.num_tiles - 1 : t, ph, n, y0, x0);
+            tile_coords(p, t, ph, n, y0, x0);
             int gy = y0 + dy, gx = x0 + dx;
-            bool valid = gy < p.gh && gx < p.gw && !phantom;
+            bool valid = gy < p.gh && gx < p.gw;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
             if (KXF) {
                 // folded column taps: this lane's row is input pixel x0 - 1 + 30 q + lane; lanes
@@ -867,7 +853,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int m = 0; m < MT; ++m) {
                 const int rb = m * 128 + q * 32, rm = rb + lane;
                 const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
-                const bool valid = gy < p.gh && gx < p.gw && !phantom;
+                const bool valid = gy < p.gh && gx < p.gw;
                 const int by = y0 + (rb >> p.tw_log), bx = x0 + (rb & (tw - 1));
                 const uint32_t tb = tbase + m * BN;
 #pragma unroll 1
@@ -937,7 +923,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     ptx::fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0 && !phantom) {
+                    if (lane == 0) {
                         if (p.mode == MODE_T)
                             ptx::tma_store_5d(&tmC, sbuf, (ph & 1) * p.out_cs + p.out_coff + k0, bx, ph >> 1, by, n);
                         else if (t3) // phase k0 / C_out: output row parity >> 1, column parity & 1
@@ -956,7 +942,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // row block m of the tile: accumulator m, pixel rows m * 128 + lane row
             const int rm = m * 128 + row;
             const int gy = y0 + (rm >> p.tw_log), gx = x0 + (rm & (tw - 1));
-            const bool valid = gy < p.gh && gx < p.gw && !phantom;
+            const bool valid = gy < p.gh && gx < p.gw;
             const uint32_t tb = tbase + m * BN;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 16) {
@@ -1045,7 +1031,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     ptx::tc_fence_before();
     __syncthreads();
-    if (MC) ptx::cluster_sync(); // neither CTA leaves while the other may still signal it
     if (warp == 1) {
         __syncwarp();
         ptx::tc_fence_after();
@@ -1211,7 +1196,7 @@ template <int BN, int CK, int TS, int F8 = 0, int RES = 0>
 int launch_halo_grp(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                     cudaStream_t st) {
     using C = HaloGrpCfg<BN, CK, TS, F8, RES>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, TS, 0, RES ? 2 : 1>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, TS, RES ? 2 : 1>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1248,7 +1233,7 @@ template <int BN, int CK, int F8, int NCK> struct KxfCfg {
 template <int BN, int CK, int F8, int NCK>
 int launch_kxf(const CUtensorMap &ma, const CUtensorMap &mk, const TcParams &p, cudaStream_t st) {
     using C = KxfCfg<BN, CK, F8, NCK>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, 0, 0, 2, 0, NCK>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, F8, 1, 2, 0, 2, 0, NCK>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1267,12 +1252,12 @@ int launch_kxf(const CUtensorMap &ma, const CUtensorMap &mk, const TcParams &p, 
     return FVV_OK;
 }
 
-template <int BN, int F8, int TS, int MC, int MT = 1>
+template <int BN, int F8, int TS, int MT = 1>
 int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const TcParams &p,
                 cudaStream_t st) {
     using C = HaloCfg<BN, TS, MT>;
     constexpr int CK = F8 ? 128 : 64;
-    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8, 1, C::STAGES_B, TS, MC>;
+    auto kern = conv_tc_kernel<BN, CK, MT, C::STAGES, C::CTAS, F8, 1, C::STAGES_B, TS>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1284,26 +1269,6 @@ int launch_halo(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap 
         FVV_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
     int slots = g_num_sms * C::CTAS;
-    if (MC) {
-        // clusters of two CTAs, tiles in pairs: an even grid over the even tile count
-        slots &= ~1;
-        const int pairs_x2 = (p.num_tiles + 1) & ~1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(pairs_x2 < slots ? pairs_x2 : slots);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = C::SMEM;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        FVV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, mc, p));
-        count_launch();
-        return FVV_OK;
-    }
     int grid = p.num_tiles < slots ? p.num_tiles : slots;
     kern<<<grid, kThreads, C::SMEM, st>>>(ma, mb, mc, p);
     count_launch();
@@ -1321,30 +1286,29 @@ bool halo_ok(int bn, int ck, int es, bool f8) {
     return !f8 && ((bn == 16 && ck == 16) || (bn == 32 && ck == 32));
 }
 
-// N = 256 runs as cluster pairs sharing the weight slices (mb_half: box of 128 rows)
 // (mb3: box of 3 taps, for the grouped stages)
 template <int TS>
-int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+int dispatch_halo_ts(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb,
                      const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
-    if (f8) // the 256-channel convs as cluster pairs; the all-phase t1 (N = 32) on grouped stages
+    if (f8) // the 256-channel convs; the all-phase t1 (N = 32) on grouped stages
         return bn == 32 ? launch_halo_grp<32, 128, TS, 1>(ma, mb3, mc, p, st)
-                        : launch_halo<256, 1, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
+                        : launch_halo<256, 1, TS, kHaloMT256>(ma, mb, mc, p, st);
     // the 16 / 32-channel convs (one channel block): weight slices resident
     if (ck == 16) return launch_halo_grp<16, 16, TS, 0, 1>(ma, mb3, mc, p, st);
     if (ck == 32) return launch_halo_grp<32, 32, TS, 0, 1>(ma, mb3, mc, p, st);
     switch (bn) {
     case 32: return launch_halo_grp<32, 64, TS>(ma, mb3, mc, p, st);
     case 64: return p.mode == MODE_T3 && !TS ? launch_halo_grp<64, 64, 0, 0, 1>(ma, mb3, mc, p, st)
-                                             : launch_halo<64, 0, TS, 0>(ma, mb, mc, p, st);
-    case 128: return launch_halo<128, 0, TS, 0>(ma, mb, mc, p, st);
-    default: return launch_halo<256, 0, TS, 1, kHaloMT256>(ma, mb_half, mc, p, st);
+                                             : launch_halo<64, 0, TS>(ma, mb, mc, p, st);
+    case 128: return launch_halo<128, 0, TS>(ma, mb, mc, p, st);
+    default: return launch_halo<256, 0, TS, kHaloMT256>(ma, mb, mc, p, st);
     }
 }
 
-int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mb_half,
+int dispatch_halo(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &mb,
                   const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p, cudaStream_t st) {
-    return p.tma_store ? dispatch_halo_ts<1>(bn, ck, f8, ma, mb, mb_half, mb3, mc, p, st)
-                       : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb_half, mb3, mc, p, st);
+    return p.tma_store ? dispatch_halo_ts<1>(bn, ck, f8, ma, mb, mb3, mc, p, st)
+                       : dispatch_halo_ts<0>(bn, ck, f8, ma, mb, mb3, mc, p, st);
 }
 
 // Stride-2 pair halo: an A ring of 129-pair boxes, the nine weight slices resident.
@@ -1365,7 +1329,7 @@ template <int BN, int CK, int TS>
 int launch_s2h(const CUtensorMap &ma, const CUtensorMap &mb3, const CUtensorMap &mc, const TcParams &p,
                cudaStream_t st) {
     using C = S2hCfg<BN, CK, TS>;
-    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 0, C::STAGES, TS, 0, 0, 1>;
+    auto kern = conv_tc_kernel<BN, CK, 1, C::STAGES, C::CTAS, 0, 0, C::STAGES, TS, 0, 1>;
     static bool attr_set = false;
     if (!attr_set) {
         FVV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -1533,10 +1497,6 @@ int tc_prepare(fvv_interp *h, const float *blob) {
             FVV_TRY(encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, ck * 2));
             box[2] = 1;
         }
-        if (cop == 256) {
-            box[1] = (cuuint32_t)(cop / 2);
-            FVV_TRY(encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, ck * 2));
-        }
         if (tc_kxf_layer(i)) folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
     }
     // folded copies allocated after every layer's own weights: the per-layer weight
@@ -1633,8 +1593,6 @@ int tc_prepare_fp8(fvv_interp *h, const float *blob) {
         int rc = taps == 9 ? encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, 128) : FVV_OK;
         box[2] = 1;
         if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map, 3, tw.w, dims, strides, box, 128);
-        box[1] = (cuuint32_t)(rows / 2);
-        if (rc == FVV_OK) rc = encode((CUtensorMap *)tw.map_half, 3, tw.w, dims, strides, box, 128);
         g_encode_u8 = false;
         FVV_TRY(rc);
     }
@@ -1713,6 +1671,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.out = out; p.out_cs = out_cs; p.out_coff = out_coff;
     p.bias = h->bias + h->b_off[li];
     p.err = h->d_err;
+    p.stall_cycles = h->stall_now;
     if (epi) {
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them
@@ -1791,7 +1750,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         return p.tma_store ? dispatch_s2h_ts<1>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st)
                            : dispatch_s2h_ts<0>(bn, ck, ma, *(const CUtensorMap *)tw.map3, mc, p, st);
     if (halo)
-        return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map, *(const CUtensorMap *)tw.map_half,
+        return dispatch_halo(bn, ck, f8, ma, *(const CUtensorMap *)tw.map,
                              *(const CUtensorMap *)tw.map3, mc, p, st);
     if (p.mode == MODE_S2 && !f8 && tw.wcopies > 1) {
         p.wcopies = tw.wcopies;

@@ -665,8 +665,20 @@ int fvv_interp_layer(fvv_interp *h, int layer, const void *in, int in_cs, int in
     }
     if (L.kind == K_CONV && L.stride == 2 && (H % 2 || W % 2)) { set_error("stride-2 layer needs even H, W"); return FVV_ESHAPE; }
     g_launches = 0;
-    return conv(h, layer, in, in_cs, in_coff, n, H, W, out, out_cs, out_coff, out_f32 != 0 || !is_bf16(h),
-                (cudaStream_t)stream);
+    h->stall_now = h->stall_cycles;
+    h->stall_cycles = 0;
+    int rc = conv(h, layer, in, in_cs, in_coff, n, H, W, out, out_cs, out_coff, out_f32 != 0 || !is_bf16(h),
+                  (cudaStream_t)stream);
+    h->stall_now = 0;
+    return rc;
+}
+
+int fvv_interp_inject_stall(fvv_interp *h, long long cycles) {
+    clear_error();
+    if (!h) { set_error("NULL handle"); return FVV_EINVAL; }
+    if (cycles < 1000 || cycles > (1ll << 31)) { set_error("stall limit %lld outside [1000, 2^31] cycles", cycles); return FVV_EINVAL; }
+    h->stall_cycles = cycles;
+    return FVV_OK;
 }
 
 int fvv_interp_status(fvv_interp *h) {

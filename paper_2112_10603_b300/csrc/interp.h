@@ -35,7 +35,6 @@ struct TcWeights {
     void *w = nullptr;      // device, [phase*taps][Co_pad][Ci_pad] bf16 (or fp8) K-major
     float *scale = nullptr; // FP8: per-output-channel dequantisation scale
     alignas(64) unsigned char map[128] = {}; // host CUtensorMap of w (B operand)
-    alignas(64) unsigned char map_half[128] = {}; // same, box of C_out / 2 rows (cluster-pair loads)
     alignas(64) unsigned char map3[128] = {};     // same, box of 3 consecutive taps (grouped halo stages)
     // folded column taps: per row tap ky one slice of kxf_n rows (kx * G + j, G = output
     // columns per tap), [3][kxf_n][Ci_pad]; map_k boxes the 3 row taps of one channel block
@@ -85,6 +84,9 @@ struct fvv_interp {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     long long host_calls = 0;
     int *d_err = nullptr; // device error word written by bounded waits
+    // fault injection (fvv_interp_inject_stall): armed for the next fvv_interp_layer call,
+    // live (stall_now) only during that call, so no captured graph ever holds it
+    long long stall_cycles = 0, stall_now = 0;
     size_t dev_bytes = 0;
     int last_launches = 0;
     std::vector<void *> allocs;

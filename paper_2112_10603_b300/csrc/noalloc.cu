@@ -13,7 +13,11 @@
 // rows.  That repacked copy is the only scratch memory the call needs; it lives in
 // a fixed file-scope device array (g_noalloc_w, 4 MiB: the largest layer of
 // Table 3, RefineNet's d0 with 512 x 128 x 16 weights).  Every GPU that loads the
-// library holds this array until the process exits.
+// library holds this array until the process exits.  The CUDA runtime loads this
+// file's module lazily: the first call on a device loads it, which is when the driver
+// creates the array on that device (an allocation the driver makes, and one that may
+// synchronise the device), and that call also looks up the array's address.  Calls
+// after the first on a device allocate nothing.
 #include <mutex>
 
 #include "interp.h"
@@ -105,9 +109,18 @@ extern "C" int fvv_layer_noalloc(int layer, const float *w, const float *b, cons
         set_error("fvv_layer_noalloc: stride-2 layer %s needs even H, W", L.name);
         return FVV_ESHAPE;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    // the scratch address below is the current device's; a stream of another device
+    // would have the kernels read and write that device's copy of the array
+    int cur = -1, sdev = -1;
+    FVV_CHECK_CUDA(cudaGetDevice(&cur));
+    FVV_CHECK_CUDA(cudaStreamGetDevice(st, &sdev));
+    if (sdev != cur) {
+        set_error("fvv_layer_noalloc: stream belongs to device %d, current device is %d", sdev, cur);
+        return FVV_EINVAL;
+    }
     float *scratch = nullptr;
     FVV_TRY(noalloc_scratch(&scratch));
-    cudaStream_t st = (cudaStream_t)stream;
     noalloc_repack_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, L.kind == K_CONVT, L.ci, L.co, scratch);
     FVV_CHECK_CUDA(cudaGetLastError());
     ConvArgs a{};

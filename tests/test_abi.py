@@ -59,3 +59,14 @@ def test_create_rejects_bad_arguments(lib, H, W, opts, code):
 def test_default_opts(lib):
     o = fvv.fvv_default_opts()
     assert (o.precision, o.pad_mode, o.t_mode, o.max_views, o.max_cams) == (0, 0, 0, 16, 2)
+
+
+def test_noalloc_source_allocates_nothing():
+    """The allocation-free entry point's source calls no device allocator (its only
+    scratch is a file-scope __device__ array)."""
+    src = open(os.path.join(ROOT, "paper_2112_10603_b300", "csrc", "noalloc.cu")).read()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    for banned in ("cudaMalloc", "cudaFree", "cuMemAlloc", "cuMemFree", "dalloc", "torch", "new ", "malloc("):
+        assert banned not in code, banned
+    assert re.search(r"static\s+__device__\s+__align__\(256\)\s+float\s+g_noalloc_w\[", code)
+    assert "cudaGetSymbolAddress" in code

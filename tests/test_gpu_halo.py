@@ -8,8 +8,8 @@ column taps read it 0, 1, 2 rows in.  Checks:
 * each such layer (128-, 64- and 32-byte operand rows) alone on wide ragged grids (last tile partly outside the
   grid, zero padding on both sides) against the oracle's conv of the same
   bf16-rounded input and weights, the bar of the per-layer tests;
-* the 256-channel layers run as clusters of two CTAs sharing each weight slice
-  (each loads one half and multicasts it): odd tile counts included;
+* the 256-channel layers on an odd tile count (one CTA per SM, each loading its
+  own weight slices; a persistent CTA's last tile may be its only one);
 * the stride-2 convs with 16/32-channel input pixels (one box of 129 pixel pairs per
   row tap, resident weights) on ragged grids against the oracle;
 * the whole BF16 forward with the halo tiles equals, bit for bit, the same
@@ -70,8 +70,7 @@ def test_halo_layer_matches_oracle(torch_cuda, name):
     # grid widths 260 = 2 x 128 + 4 (conv) and 131 = 128 + 3 (transposed conv input);
     # vib1.t1: 370 = 3 x 120 + 10 (four tiles of the folded column taps, grids >= 256)
     H, W = ((3, 370) if name == "vib1.t1" else (3, 131)) if kind == "convT" else (3, 260)
-    # one image of vib2.m0: 3 x 3 = 9 tiles, an odd count for the 256-channel layers'
-    # cluster pairs (the last pair's second tile is a filler that must not be stored)
+    # one image of vib2.m0: 3 x 3 = 9 tiles, an odd tile count for a 256-channel layer
     n = 1 if name == "vib2.m0" else 2
     cs = ci + (64 if li % 2 else 0)        # a wider pixel stride and a channel offset
     coff = 64 if li % 2 else 0
