@@ -4,16 +4,19 @@
   output buffer, the t values and the camera frames change between replays;
 * autotuned tile rectangles change no output bit (every output element keeps the
   same K-loop order whatever the tile) and the JSON cache round-trips;
-* a rig instant with uneven per-pair view counts (one batch) equals per-pair runs.
+* a rig instant with uneven per-pair view counts (one batch) equals per-pair runs;
+* every view of such a rig instant matches the FP64 oracle's view of its pair:
+  FP32 path max |err| <= 1e-4, BF16 path PSNR >= 45 dB.
 """
 import json
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2112_10603_b300 as fvv
 from synth import scene
-from tests.gpu_common import blob, pair
+from tests.gpu_common import blob, pair, psnr
 
 pytestmark = pytest.mark.gpu
 
@@ -77,3 +80,31 @@ def test_rig_instant_uneven_counts(torch_cuda):
     for p in range(4):
         ref = one.run(cams[p], cams[p + 1], ts[offs[p]:offs[p + 1]]).cpu().numpy()
         np.testing.assert_array_equal(out[offs[p]:offs[p + 1]], ref)
+
+
+def test_rig_instant_matches_oracle(torch_cuda):
+    """A batched rig instant (4 pairs of a 5-camera arc, uneven view counts, random t)
+    against the FP64 oracle, view by view, on the FP32 and the BF16 path."""
+    torch = torch_cuda
+    H, W = 48, 80
+    frames = scene.rig(15, H, W, n_cams=5, max_disp=6.0)
+    cams = [torch.from_numpy(c).cuda() for c in frames]
+    rng = np.random.default_rng(15)
+    counts = [2, 1, 3, 1]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    ts = np.concatenate([np.sort(rng.uniform(0, 1, c)) for c in counts]).astype(np.float32)
+    refs = []
+    for p in range(4):
+        for v in range(offs[p], offs[p + 1]):
+            refs.append(oracle.vinet_forward(blob(), frames[p], frames[p + 1], float(ts[v])))
+    for precision in (fvv.FVV_FP32, fvv.FVV_BF16):
+        it = fvv.Interpolator(blob(), H, W, precision=precision, max_views=8, max_cams=5)
+        out = it.run_batch(cams, [0, 1, 2, 3], offs, ts).cpu().numpy()
+        fvv.fvv_interp_status(it.h)
+        for v, ref in enumerate(refs):
+            if precision == fvv.FVV_FP32:
+                err = float(np.abs(out[v] - ref).max())
+                assert err <= 1e-4, (v, err)
+            else:
+                assert psnr(out[v], ref) >= 45.0, (v, psnr(out[v], ref))
+        it.close()

@@ -1,16 +1,19 @@
 """The server on the GPU: every result of a mixed-resolution, mixed-pair request mix
 equals the same view computed alone by an interpolator (bit for bit: the batch is
 one forward over independent views, and each output element's arithmetic does not
-depend on its neighbours in the batch)."""
+depend on its neighbours in the batch), and matches the FP64 oracle's view of the
+same pair and t (BF16: PSNR >= 45 dB).  In dense mode the served views are those of
+the snapped t = k / 2^n, again against the interpolator alone and the oracle."""
 import ctypes
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2112_10603_b300 as fvv
 from synth import scene
-from tests.gpu_common import blob
+from tests.gpu_common import blob, psnr
 
 pytestmark = pytest.mark.gpu
 
@@ -29,8 +32,8 @@ def test_server_mix_matches_alone():
     from paper_2112_10603_b300 import build as fvv_build
     fvv_build.build()
     sizes = [(48, 80), (64, 96)]
-    cams = {r: [torch.from_numpy(c).cuda() for c in scene.rig(20 + r, h, w, n_cams=3, max_disp=6.0)]
-            for r, (h, w) in enumerate(sizes)}
+    frames = {r: scene.rig(20 + r, h, w, n_cams=3, max_disp=6.0) for r, (h, w) in enumerate(sizes)}
+    cams = {r: [torch.from_numpy(c).cuda() for c in frames[r]] for r in frames}
     cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=2, res_h=[h for h, _ in sizes],
                                     res_w=[w for _, w in sizes], n_cams=3, slots_per_res=2, max_batch=3,
                                     pool_views=16)
@@ -58,6 +61,8 @@ def test_server_mix_matches_alone():
             got = _fetch(ptr, (h, w, 3))
             ref = alone[r].run(cams[r][p], cams[r][p + 1], [t]).cpu().numpy()[0]
             np.testing.assert_array_equal(got, ref)
+            ref64 = oracle.vinet_forward(blob(), frames[r][p], frames[r][p + 1], t)
+            assert psnr(got, ref64) >= 45.0, (r, p, t, psnr(got, ref64))
             assert lat > 0
             assert fvv.fvv_serve_release(s, tk) == 0
         st = fvv.fvv_serve_stats_get(s)
@@ -74,8 +79,8 @@ def test_dense_mode_views_match_alone():
     from paper_2112_10603_b300 import build as fvv_build
     fvv_build.build()
     h, w = 48, 80
-    frames = [[torch.from_numpy(c).cuda() for c in scene.rig(30 + i, h, w, n_cams=3, max_disp=6.0)]
-              for i in range(2)]
+    frames_np = [scene.rig(30 + i, h, w, n_cams=3, max_disp=6.0) for i in range(2)]
+    frames = [[torch.from_numpy(c).cuda() for c in f] for f in frames_np]
     cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=1, res_h=[h], res_w=[w], n_cams=3,
                                     slots_per_res=2, max_batch=6, dense_levels=2)
     s = fvv.fvv_serve_create(blob(), cfg)
@@ -99,6 +104,8 @@ def test_dense_mode_views_match_alone():
                     ref = cams[p if k == 0 else p + 1].cpu().numpy()
                 else:
                     ref = alone.run(cams[p], cams[p + 1], [k / 4]).cpu().numpy()[0]
+                    ref64 = oracle.vinet_forward(blob(), frames_np[inst][p], frames_np[inst][p + 1], k / 4)
+                    assert psnr(got, ref64) >= 45.0, (inst, p, t, psnr(got, ref64))
                 np.testing.assert_array_equal(got, ref)
                 fvv.fvv_serve_release(s, tk)
             st = fvv.fvv_serve_stats_get(s)
