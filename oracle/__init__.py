@@ -61,6 +61,11 @@ def lib():
         L.oracle_layer_info.argtypes = [I] + [ctypes.POINTER(ctypes.c_int)] * 5
         L.oracle_vinet_forward.argtypes = [F, ctypes.c_long, F, F, I, I, ctypes.c_double, I, D,
                                            ctypes.c_void_p]
+        L.oracle_lap_loss.argtypes = [D, D, I, I, I, I, D]
+        L.oracle_lap_loss.restype = ctypes.c_double
+        L.oracle_lap_down.argtypes = [D, I, I, I, D]
+        L.oracle_lap_up.argtypes = [D, I, I, I, I, I, D]
+        L.oracle_lap_levels.argtypes = [D, I, I, I, I, D]
         _lib = L
     return _lib
 
@@ -209,3 +214,51 @@ def stitch_cluster(center, side_views, scale):
         r, q = divmod(k, scale)
         out[H + r * th:H + (r + 1) * th, q * tw:(q + 1) * tw] = small
     return out
+
+
+def lap_down(g):
+    """One reduction step of the Laplace pyramid of Eq. 3: binomial [1 4 6 4 1]/16
+    blur (edges replicated) sampled at even pixels; H x W x C -> ceil(H/2) x ceil(W/2) x C."""
+    g = _c64(g)
+    H, W, C = g.shape
+    out = np.empty(((H + 1) // 2, (W + 1) // 2, C))
+    lib().oracle_lap_down(_d(g), H, W, C, _d(out))
+    return out
+
+
+def lap_up(g, H, W):
+    """One expansion step: the zero-inserted image filtered by 4 k k^T, at size H x W."""
+    g = _c64(g)
+    h, w, C = g.shape
+    out = np.empty((H, W, C))
+    lib().oracle_lap_up(_d(g), h, w, C, H, W, _d(out))
+    return out
+
+
+def lap_levels(img, levels=5):
+    """[L^1, ..., L^levels] of one H x W x C image (L^levels = the last G)."""
+    img = _c64(img)
+    H, W, C = img.shape
+    sizes = []
+    h, w = H, W
+    for _ in range(levels):
+        sizes.append((h, w))
+        h, w = (h + 1) // 2, (w + 1) // 2
+    out = np.empty(sum(a * b for a, b in sizes) * C)
+    lib().oracle_lap_levels(_d(img), H, W, C, levels, _d(out))
+    res, off = [], 0
+    for a, b in sizes:
+        res.append(out[off:off + a * b * C].reshape(a, b, C))
+        off += a * b * C
+    return res
+
+
+def lap_loss(pred, gt, levels=5):
+    """Laplacian-pyramid loss of Eq. 3 (Sec. 3.1) for one image pair, in float64:
+    sum_i 2^(i-1) || L^i(pred) - L^i(gt) ||_1 (L1 = sum over pixels and channels).
+    Returns (loss, [norm of level 1, ..., norm of level `levels`])."""
+    a, b = _c64(pred), _c64(gt)
+    H, W, C = a.shape
+    norms = np.empty(levels)
+    loss = lib().oracle_lap_loss(_d(a), _d(b), H, W, C, levels, _d(norms))
+    return float(loss), norms

@@ -509,3 +509,125 @@ int oracle_vinet_forward(const float *blob, long n_floats, const float *left, co
     for (int s = 0; s < 2; ++s) { free(P[s][0]); free(P[s][1]); free(I[s]); }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Laplacian-pyramid loss, Eq. 3 (Sec. 3.1 "Loss functions"):                 */
+/*   L_Lap = sum_{i=1..5} 2^(i-1) || L^i(I_hat) - L^i(I_gt) ||_1              */
+/* The paper names a five-level Laplace pyramid and no filter; the reading:   */
+/* the Burt-Adelson pyramid with the binomial kernel k = [1 4 6 4 1] / 16 and */
+/* replicated edges,                                                          */
+/*   G^1 = I,  G^(i+1)(y, x) = sum_{a,b} k[a] k[b] G^i(cl(2y+a-2), cl(2x+b-2)) */
+/*             of size ceil(H/2) x ceil(W/2);                                 */
+/*   up(G)(y, x) = sum_{a,b} 4 k[a] k[b] [y+a-2 even][x+b-2 even]             */
+/*                 G(cl((y+a-2)/2), cl((x+b-2)/2)) at the finer size;          */
+/*   L^i = G^i - up(G^(i+1)) for i < 5, L^5 = G^5;                            */
+/*   ||.||_1 = sum of |.| over every pixel and channel of the level.          */
+/* Both pyramids are built in full, then compared level by level.             */
+
+static const double LAPK[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+
+static double *lap_down(const double *g, int H, int W, int C, int *Ho, int *Wo) {
+    int h = (H + 1) / 2, w = (W + 1) / 2;
+    double *out = dalloc((size_t)h * w * C);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x)
+            for (int c = 0; c < C; ++c) {
+                double s = 0.0;
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) {
+                        int64_t yy = clampi(2 * y + a - 2, H), xx = clampi(2 * x + b - 2, W);
+                        s += LAPK[a] * LAPK[b] * g[(yy * W + xx) * C + c];
+                    }
+                out[((size_t)y * w + x) * C + c] = s;
+            }
+    *Ho = h; *Wo = w;
+    return out;
+}
+
+/* up(G) at the finer size H x W, G of size h x w */
+static double *lap_up(const double *g, int h, int w, int C, int H, int W) {
+    double *out = dalloc((size_t)H * W * C);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int c = 0; c < C; ++c) {
+                double s = 0.0;
+                for (int a = 0; a < 5; ++a) {
+                    int yy = y + a - 2;
+                    if (yy & 1) continue;               /* odd rows of the zero-inserted image */
+                    for (int b = 0; b < 5; ++b) {
+                        int xx = x + b - 2;
+                        if (xx & 1) continue;
+                        int64_t gy = clampi(yy / 2, h), gx = clampi(xx / 2, w);
+                        s += 4.0 * LAPK[a] * LAPK[b] * g[(gy * w + gx) * C + c];
+                    }
+                }
+                out[((size_t)y * W + x) * C + c] = s;
+            }
+    return out;
+}
+
+/* pyr[0..levels-1] = L^1 .. L^levels of img (H x W x C); sizes in hs, ws */
+static void lap_pyramid(const double *img, int H, int W, int C, int levels, double **pyr, int *hs, int *ws) {
+    double *g = dalloc((size_t)H * W * C);
+    memcpy(g, img, sizeof(double) * H * W * C);
+    int h = H, w = W;
+    for (int i = 0; i < levels; ++i) {
+        hs[i] = h; ws[i] = w;
+        if (i == levels - 1) { pyr[i] = g; break; }        /* L^5 = G^5 */
+        int h2, w2;
+        double *g2 = lap_down(g, h, w, C, &h2, &w2);
+        double *u = lap_up(g2, h2, w2, C, h, w);
+        for (size_t k = 0; k < (size_t)h * w * C; ++k) g[k] -= u[k];   /* L^i = G^i - up(G^(i+1)) */
+        free(u);
+        pyr[i] = g;
+        g = g2; h = h2; w = w2;
+    }
+}
+
+/* Eq. 3 for one image pair; norms[i] = || L^(i+1)(a) - L^(i+1)(b) ||_1 */
+double oracle_lap_loss(const double *a, const double *b, int H, int W, int C, int levels, double *norms) {
+    double *pa[16], *pb[16];
+    int hs[16], ws[16];
+    if (levels < 1 || levels > 16) return -1.0;
+    lap_pyramid(a, H, W, C, levels, pa, hs, ws);
+    lap_pyramid(b, H, W, C, levels, pb, hs, ws);
+    double loss = 0.0;
+    for (int i = 0; i < levels; ++i) {
+        double s = 0.0;
+        for (size_t k = 0; k < (size_t)hs[i] * ws[i] * C; ++k) s += fabs(pa[i][k] - pb[i][k]);
+        if (norms) norms[i] = s;
+        loss += ldexp(s, i);                              /* 2^(i-1), i counted from 1 */
+        free(pa[i]); free(pb[i]);
+    }
+    return loss;
+}
+
+/* The pyramid's steps, exposed for their own checks: one reduction step
+ * (G^i -> G^(i+1), out ceil(H/2) x ceil(W/2)) and one expansion step (up). */
+void oracle_lap_down(const double *g, int H, int W, int C, double *out) {
+    int h, w;
+    double *d = lap_down(g, H, W, C, &h, &w);
+    memcpy(out, d, sizeof(double) * h * w * C);
+    free(d);
+}
+
+void oracle_lap_up(const double *g, int h, int w, int C, int H, int W, double *out) {
+    double *u = lap_up(g, h, w, C, H, W);
+    memcpy(out, u, sizeof(double) * H * W * C);
+    free(u);
+}
+
+/* L^1 .. L^levels of one image, concatenated level by level */
+void oracle_lap_levels(const double *img, int H, int W, int C, int levels, double *out) {
+    double *p[16];
+    int hs[16], ws[16];
+    if (levels < 1 || levels > 16) return;
+    lap_pyramid(img, H, W, C, levels, p, hs, ws);
+    size_t off = 0;
+    for (int i = 0; i < levels; ++i) {
+        size_t n = (size_t)hs[i] * ws[i] * C;
+        memcpy(out + off, p[i], sizeof(double) * n);
+        off += n;
+        free(p[i]);
+    }
+}

@@ -119,6 +119,18 @@ def stereo_pair(seed: int, H: int, W: int, max_disp: float):
     return left, right
 
 
+def stereo_views(seed: int, H: int, W: int, max_disp: float, ts):
+    """(left, right, [view at t for t in ts]): the pair of stereo_pair and the same
+    scene seen from the camera at X = -b/2 + t b between them (the ground truth a
+    virtual view at t is compared with)."""
+    sc = Scene(seed, W)
+    b = 2.0 * max_disp / sc.f
+    left = sc.render(H, W, (-b / 2, 0.0, 0.0))
+    right = sc.render(H, W, (b / 2, 0.0, 0.0))
+    mids = [sc.render(H, W, (-b / 2 + float(t) * b, 0.0, 0.0)) for t in ts]
+    return left, right, mids
+
+
 def rig(seed: int, H: int, W: int, n_cams: int = 9, max_disp: float = 64.0):
     """n_cams views on a horizontal arc fixating (0, 0, 6); list of HxWx3 arrays."""
     sc = Scene(seed, W)
