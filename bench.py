@@ -332,28 +332,57 @@ def serve_measure(seconds, sweep=False):
 
 
 def run_serve_dense(args, rank, world, local):
-    """Dense serving (the paper's per-instant view set): 9-camera rig at 1080p, new
-    frames every 1/30 s (two frame sets alternating), 2^4 - 1 = 15 views per pair
-    rendered once per instant; users' requests snap t to k/16 and are answered from
-    the newest complete set.  Run at 4 and at 64 users: the GPU work per instant
-    (instants/s, views rendered/s) should not depend on the user count."""
+    """--workload serve-dense: the per-instant dense serving runs alone (BF16, 15 views
+    per pair, requests answered by the first set after they arrive) at 4 and 64 users,
+    and the immediate-answer configuration of the default line."""
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    torch.cuda.set_device(local)
+    line = serve_dense_measure(args.serve_seconds, "bf16", 4, False, users=(4, 64, 4))
+    line["immediate_fp8_n3"] = serve_dense_measure(args.serve_seconds, "fp8", 3, True, users=(64,))
+    line["n_gpus"] = world
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serve_dense_measure(seconds, precision, levels, immediate, users=(64,)):
+    """Dense serving (the paper's per-instant view set, Sec. 3.2 / 4.2): 9-camera rig at
+    1080p, new frames every 1/30 s (two frame sets alternating), 2^levels - 1 views per
+    pair rendered once per instant; users' requests snap t to k / 2^levels.  immediate:
+    every request is answered at once from the newest complete set, and the content's
+    age (set_frames -> answer) and staleness (instants behind the newest frames) are
+    reported beside the request latency.  The GPU work per instant does not depend on
+    the user count."""
     import threading
     import torch
     import paper_2112_10603_b300 as fvv
-    from paper_2112_10603_b300 import build as fvv_build
     from synth import scene, weights
-    fvv_build.build()
-    torch.cuda.set_device(local)
     n_cams, (h, w) = 9, (1080, 1920)
+    nd = 2 ** levels - 1
     frames = [[torch.from_numpy(c).cuda() for c in scene.rig(5 + i, h, w, n_cams=n_cams, max_disp=MAX_DISP)]
               for i in range(2)]
-    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_BF16, n_res=1, res_h=[h], res_w=[w], n_cams=n_cams,
-                                    slots_per_res=2, max_batch=15, dense_levels=4)
+    prec = {"bf16": fvv.FVV_BF16, "fp8": fvv.FVV_FP8}[precision]
+    cfg = fvv.fvv_serve_default_cfg(precision=prec, n_res=1, res_h=[h], res_w=[w], n_cams=n_cams,
+                                    slots_per_res=2, max_batch=2 * nd if nd <= 8 else nd, dense_levels=levels,
+                                    dense_immediate=int(immediate))
     s = fvv.fvv_serve_create(weights.he_init(WEIGHT_SEED), cfg)
     runs = []
     try:
+        if prec == fvv.FVV_FP8:
+            cal = []
+            for sd in range(100, 108):
+                cal += list(scene.stereo_pair(sd, h, w, MAX_DISP))
+            cal_d = torch.from_numpy(np.stack(cal)).cuda()
+            fvv.fvv_serve_calibrate_fp8(s, 0, cal_d, 8)
+            del cal_d
         fvv.fvv_serve_set_frames(s, 0, 0, frames[0])
-        for users, secs in ((4, 3.0), (64, args.serve_seconds), (4, 3.0)):
+        t0 = time.perf_counter()
+        while fvv.fvv_serve_stats_get(s)["dense_instants"] < 1:    # the first set (graph capture included)
+            if time.perf_counter() - t0 > 120:
+                raise RuntimeError("dense server: first instant did not render within 120 s")
+            time.sleep(0.005)
+        for n_users in users:
             stop = threading.Event()
             inst = [1]
 
@@ -367,30 +396,49 @@ def run_serve_dense(args, rank, world, local):
             base = fvv.fvv_serve_stats_get(s)
             th.start()
             t0 = time.perf_counter()
-            r = serve_once_dense(s, fvv, users, 30.0, secs, 7 + users, n_cams - 1)
+            r = serve_once_dense(s, fvv, n_users, 30.0, seconds if n_users == max(users) else 3.0, 7 + n_users,
+                                 n_cams - 1)
             stop.set()
             th.join()
             wall = time.perf_counter() - t0
             st = fvv.fvv_serve_stats_get(s)
             r["instants_per_s"] = (st["dense_instants"] - base["dense_instants"]) / wall
-            r["views_rendered_per_s"] = r["instants_per_s"] * (n_cams - 1) * 15
+            r["views_rendered_per_s"] = r["instants_per_s"] * (n_cams - 1) * nd
             r["frames_offered_per_s"] = (inst[0] - 1) / wall
+            if immediate:
+                # content age and staleness over this server's whole life (first set excluded: nothing
+                # is answered while it renders, since requests start after it)
+                r["content_age_p50_ms"], r["content_age_p99_ms"] = st["age_p50_ms"], st["age_p99_ms"]
+                r["stale_instants_mean"], r["stale_instants_max"] = st["stale_mean"], st["stale_max"]
             runs.append(r)
     finally:
         fvv.fvv_serve_destroy(s)
-    main = runs[1]
-    line = {"metric": "dense serving: virtual views rendered/s (9-camera rig, 1080p, 15 views per pair per instant)",
-            "value": main["views_rendered_per_s"], "unit": "views/s", "n_gpus": world, "higher_is_better": True,
-            "dtype": "bf16", "data": "synthetic 9-camera rig (two alternating frame sets), Poisson viewpoint requests",
-            "config": {"workload": "serve-dense: frames at 30 Hz, 8 pairs x 15 views per instant, 64 users x 30 Hz "
-                                   "requests snapped to t = k/16", "seconds": args.serve_seconds,
-                       "slots": 2, "max_batch": 15},
-            "instants_per_s": main["instants_per_s"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
-            "answered_req_per_s": main["completed_req_per_s"],
-            "user_count_invariance": [{k: r[k] for k in ("users", "instants_per_s", "views_rendered_per_s",
-                                                         "completed_req_per_s", "p50_ms", "p99_ms")} for r in runs]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    del frames
+    torch.cuda.empty_cache()
+    main = max(runs, key=lambda r: r["users"])
+    ms_per_instant = 1e3 / main["instants_per_s"] if main["instants_per_s"] > 0 else None
+    line = {"metric": f"dense serving: virtual views rendered/s (9-camera rig, 1080p, {nd} views per pair per instant)",
+            "value": main["views_rendered_per_s"], "unit": "views/s", "higher_is_better": True,
+            "dtype": {"bf16": "bf16", "fp8": "fp8e4m3+bf16"}[precision],
+            "data": "synthetic 9-camera rig (two alternating frame sets), Poisson viewpoint requests",
+            "config": {"workload": f"serve-dense: frames at 30 Hz, 8 pairs x {nd} views per instant, "
+                                   f"{main['users']} users x 30 Hz requests snapped to t = k/{nd + 1}",
+                       "seconds": seconds, "slots": 2, "precision": precision, "levels": levels,
+                       "answer": "immediate from the newest complete set" if immediate
+                                 else "first complete set after the request"},
+            "instants_per_s": main["instants_per_s"], "ms_per_instant": ms_per_instant,
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "answered_req_per_s": main["completed_req_per_s"]}
+    if immediate:
+        line.update({k: main[k] for k in ("content_age_p50_ms", "content_age_p99_ms", "stale_instants_mean",
+                                          "stale_instants_max")})
+        line["note"] = ("request latency = submit -> answer (answers come from the newest complete set); the "
+                        "content's age cannot fall below one instant's render time "
+                        f"({ms_per_instant:.0f} ms for {8 * nd} views) plus the wait for the frames it shows")
+    if len(runs) > 1:
+        line["user_count_invariance"] = [{k: r[k] for k in ("users", "instants_per_s", "views_rendered_per_s",
+                                                            "completed_req_per_s", "p50_ms", "p99_ms")} for r in runs]
+    return line
 
 
 def serve_once_dense(s, fvv, n_users, rate_hz, seconds, seed, n_pairs):
@@ -524,7 +572,7 @@ def main():
     ap.add_argument("--views", type=int, default=None,
                     help="views per step (t = k/(views+1)); default 7 (15 with --precision fp8)")
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed steps (for profiling)")
-    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve", "serve-dense", "stitch"],
+    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "serve", "serve-dense", "stitch", "lap"],
                     help="pair: the headline 1-pair 7-view step; rig: batched 9-camera instants; "
                          "serve: 64-user mixed-resolution serving")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -549,6 +597,8 @@ def main():
         return run_serve_dense(args, rank, world, local)
     if args.workload == "stitch":
         return run_stitch(args, rank, world, local)
+    if args.workload == "lap":
+        return run_lap(args, rank, world, local)
 
     import torch
     import paper_2112_10603_b300 as fvv
@@ -666,11 +716,14 @@ def main():
             if args.precision != "fp32":
                 line["parity"][f"{args.precision}_vs_fp32"] = err_psnr(out_main[mid], out32[mid])
         if args.precision == "bf16" and not args.no_more_configs:
+            out.copy_(torch.from_numpy(out_main))      # the step's BF16 views again
+            line["lap_loss"] = lap_measure(out, args.steps, flush, pk, pk_kind)
             del out
             torch.cuda.empty_cache()
             line["fp8"] = fp8_measure(blob, L, R, ref, out32[mid], args.warmup, args.steps, flush, pk, pk_kind)
             line["rig"] = rig_measure("bf16", 3, max(10, args.steps), rank)
             line["serve"] = serve_measure(args.serve_seconds)
+            line["serve_dense"] = serve_dense_measure(args.serve_seconds, "fp8", 3, True)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -768,6 +821,72 @@ def conv_roofline(precision, lms, lfl, lln, ms_prof, pk, pk_kind, views, fp8_pea
     roof["launches"] = int(lln.sum())
     roof["timed_region"] = "profiled pass of the same steps (per-layer CUDA events, direct launches)"
     return roof
+
+
+def run_lap(args, rank, world, local):
+    """--workload lap: the Laplacian-pyramid loss alone, on the bench pair's 7 ground-
+    truth views against the same views shifted by one pixel (a stand-in prediction)."""
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    from synth import scene
+    fvv_build.build()
+    torch.cuda.set_device(local)
+    _, _, mids = scene.stereo_views(rank_pair_seed(rank), H, W, MAX_DISP, TS)
+    views = torch.from_numpy(np.roll(np.stack(mids), 1, axis=2)).cuda()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    pk, pk_kind = peaks()
+    line = lap_measure(views, args.steps, flush, pk, pk_kind)
+    line["n_gpus"] = world
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def lap_measure(views, steps, flush, pk, pk_kind):
+    """The Laplacian-pyramid loss of Eq. 3 (forward) of the step's views against the
+    ground truth (the synthetic scene rendered from the camera at each t): one
+    fvv_lap_loss call over all views, timed with CUDA events after an L2 flush; HBM
+    roofline with the algorithmic bytes (both images read once, every lower pyramid
+    level written once and read once); the t = 0.5 view's loss against the oracle."""
+    import torch
+    import oracle
+    import paper_2112_10603_b300 as fvv
+    from synth import scene
+    n = views.shape[0]
+    _, _, mids = scene.stereo_views(rank_pair_seed(0), H, W, MAX_DISP, TS)
+    gt = torch.from_numpy(np.stack(mids)).cuda()
+    ws_bytes = fvv.fvv_lap_loss_workspace(n, H, W)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    loss = torch.empty(n, device="cuda")
+    norms = torch.empty((n, 5), device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        fvv.fvv_lap_loss(views, gt, n, H, W, ws, ws_bytes, loss, norms)
+    ts_ms = []
+    for _ in range(max(steps, 5)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        fvv.fvv_lap_loss(views, gt, n, H, W, ws, ws_bytes, loss, norms)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts_ms.append(a.elapsed_time(b))
+    ms = float(np.median(ts_ms))
+    lv = [(H, W)]
+    for _ in range(4):
+        lv.append(((lv[-1][0] + 1) // 2, (lv[-1][1] + 1) // 2))
+    algo = n * (2 * H * W * 12 + sum(2 * h * w * 12 for h, w in lv[1:]))
+    gbs = algo / (ms / 1e3) / 1e9
+    mid = min(range(n), key=lambda k: abs(TS[k] - 0.5))
+    got = loss.cpu().numpy()
+    ref, _ = oracle.lap_loss(views[mid].cpu().numpy().astype(np.float64), mids[mid].astype(np.float64))
+    del ws, gt
+    return {"metric": "Laplacian-pyramid loss (Eq. 3, forward) of the step's views vs ground truth",
+            "views": n, "us_per_call": ms * 1e3, "launches_per_call": 5,
+            "loss_per_view_mean": float(got.mean()),
+            "parity_t05": {"gpu": float(got[mid]), "oracle_fp64": ref, "rel_err": abs(float(got[mid]) - ref) / ref},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "algorithmic_bytes": algo,
+                         "peak_source": f"{pk_kind} hbm_gbs", "traffic": None}}
 
 
 def fp8_measure(blob, L, R, ref, view32_mid, warmup, steps, flush, pk, pk_kind):

@@ -195,6 +195,26 @@ int fvv_layer_noalloc(int layer, const float *w, const float *b, const float *in
 int fvv_stitch_cluster(const float *center, const float *const *side_views, int n_side, int H, int W, int scale,
                        float *out, void *stream);
 
+/* Laplacian-pyramid loss of Eq. 3 (Sec. 3.1 "Loss functions"), forward only, for n
+ * image pairs: loss[v] = sum_{i=1..5} 2^(i-1) || L^i(pred_v) - L^i(gt_v) ||_1, where
+ * L^i is level i of the Laplace pyramid (the paper names the pyramid, not its filter:
+ * here the Burt-Adelson pyramid of the binomial kernel [1 4 6 4 1]/16 with replicated
+ * edges, each level ceil(H/2) x ceil(W/2) of the one before, L^5 = the fifth low-pass
+ * image) and ||.||_1 sums |.| over every pixel and channel of the level.
+ *   pred, gt: DEVICE, n x H x W x 3 float32 (HWC), e.g. fvv_interp_run's views and the
+ *     ground truth;
+ *   workspace: DEVICE, at least fvv_lap_loss_workspace(n, H, W) bytes, 256-byte
+ *     aligned, owned by the caller (the lower pyramid levels and the partial sums);
+ *   loss: DEVICE, n float32 (or NULL); level_norms: DEVICE, n x 5 float32, the five
+ *     L1 norms per pair in level order (or NULL; not both NULL).
+ * The result does not depend on the launch or the order of blocks (fixed-order sums).
+ * Errors: FVV_EINVAL for NULL pointers or a short / misaligned workspace, FVV_ESHAPE
+ * unless 1 <= n <= 65535, H, W >= 2 and H x W <= 2^28.  Asynchronous on `stream`;
+ * allocates nothing. */
+size_t fvv_lap_loss_workspace(int n, int H, int W);
+int fvv_lap_loss(const float *pred, const float *gt, int n, int H, int W, void *workspace, size_t workspace_bytes,
+                 float *loss, float *level_norms, void *stream);
+
 /* Synchronise the device and report whether any bounded device-side wait of
  * this handle's kernels gave up since the last call (FVV_ETIMEOUT, flag then
  * cleared) or a CUDA error is pending (FVV_ECUDA); FVV_OK otherwise. */
@@ -277,14 +297,19 @@ void fvv_interp_destroy(fvv_interp *h);
  * other).  A request's t snaps to the nearest k / 2^n; k = 0 or 2^n answer with the
  * camera frame itself.  A request is answered at once from the newest complete set
  * when that set belongs to the newest frames (set_frames), else by the first set
- * completed after it arrives; the GPU load does not depend on the number of users.  Its view pointer stays valid until the server starts rendering the
+ * completed after it arrives; the GPU load does not depend on the number of users.
+ * With dense_immediate = 1 a request is answered at once from the newest complete set
+ * whatever instant it shows (a set exists once the first instant has rendered); the
+ * stats then give, beside the request latency, the age of the answered content (ms
+ * from the set_frames call of its instant to the answer) and its staleness (instants
+ * between it and the newest frames).  Its view pointer stays valid until the server starts rendering the
  * second instant after it; release() only forgets the ticket.  Frames passed to
  * set_frames must stay valid until their instant has been rendered. */
 
 #define FVV_SERVE_MAX_RES 4
 
 typedef struct {
-    int precision;                  /* FVV_BF16 or FVV_FP32 */
+    int precision;                  /* FVV_BF16, FVV_FP32 or FVV_FP8 (then fvv_serve_calibrate_fp8) */
     int n_res;                      /* resolutions served, 1 .. FVV_SERVE_MAX_RES */
     int res_h[FVV_SERVE_MAX_RES], res_w[FVV_SERVE_MAX_RES];
     int n_cams;                     /* cameras of the rig; pair p = cameras p, p + 1 */
@@ -294,6 +319,7 @@ typedef struct {
     size_t hbm_budget;              /* device bytes the server may hold; 0 = unlimited */
     double fake_ms_per_view;        /* > 0: no GPU, simulated batches (tests) */
     int dense_levels;               /* 0: render each request; n > 0: dense mode, 2^n - 1 views per pair */
+    int dense_immediate;            /* dense mode: 1 = answer from the newest complete set at once */
 } fvv_serve_cfg;
 
 typedef struct {
@@ -301,6 +327,9 @@ typedef struct {
     double p50_ms, p99_ms, max_ms;  /* latency submit -> view ready, completed requests */
     size_t device_bytes;
     long long dense_instants;       /* dense mode: instants whose view set was rendered */
+    double age_p50_ms, age_p99_ms;  /* dense mode: age of the answered content (set_frames -> answer) */
+    double stale_mean;              /* dense mode: mean instants between the answered set and the newest frames */
+    long long stale_max;
 } fvv_serve_stats;
 
 typedef struct fvv_server fvv_server;
@@ -311,6 +340,12 @@ void fvv_serve_default_cfg(fvv_serve_cfg *cfg);
 
 /* weights: as for fvv_interp_create (may be NULL with fake_ms_per_view > 0). */
 int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg *cfg, fvv_server **out);
+
+/* FP8 servers (precision FVV_FP8): the activation scales of every slot of resolution
+ * res_id, measured as fvv_calibrate_fp8 does (frames: DEVICE, n_pairs x 2 x H x W x 3
+ * float32 at that resolution).  Required before the first set_frames of that
+ * resolution; FVV_EBUSY if one of its slots is running. */
+int fvv_serve_calibrate_fp8(fvv_server *s, int res_id, const float *frames, int n_pairs);
 
 /* Frames of capture instant `instant` at resolution res_id: n_cams DEVICE pointers
  * (H x W x 3 float32, caller-owned, kept valid until replaced).  Batches use the

@@ -65,6 +65,9 @@ def lib():
         L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
         L.fvv_interp_status.argtypes = [_P]
         L.fvv_interp_inject_stall.argtypes = [_P, ctypes.c_longlong]
+        L.fvv_lap_loss_workspace.argtypes = [ctypes.c_int] * 3
+        L.fvv_lap_loss_workspace.restype = ctypes.c_size_t
+        L.fvv_lap_loss.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P]
         L.fvv_interp_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_char_p]
         L.fvv_layer_noalloc.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
@@ -223,6 +226,17 @@ def fvv_interp_status(h: int):
     _check(lib().fvv_interp_status(h))
 
 
+def fvv_lap_loss_workspace(n: int, H: int, W: int) -> int:
+    return int(lib().fvv_lap_loss_workspace(n, H, W))
+
+
+def fvv_lap_loss(pred, gt, n: int, H: int, W: int, workspace, workspace_bytes: int, loss, level_norms=None,
+                 stream=None):
+    """Laplacian-pyramid loss of Eq. 3 for n image pairs (device buffers, see fvv.h)."""
+    _check(lib().fvv_lap_loss(_dev(pred), _dev(gt), n, H, W, _dev(workspace), workspace_bytes, _dev(loss),
+                              _dev(level_norms), _stream(stream)))
+
+
 def fvv_interp_inject_stall(h: int, cycles: int):
     """Arm the next fvv_interp_layer call's bounded-wait fault injection (see fvv.h)."""
     _check(lib().fvv_interp_inject_stall(h, cycles))
@@ -263,14 +277,16 @@ class fvv_serve_cfg(ctypes.Structure):
                 ("res_h", ctypes.c_int * FVV_SERVE_MAX_RES), ("res_w", ctypes.c_int * FVV_SERVE_MAX_RES),
                 ("n_cams", ctypes.c_int), ("slots_per_res", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("pool_views", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("fake_ms_per_view", ctypes.c_double),
-                ("dense_levels", ctypes.c_int)]
+                ("dense_levels", ctypes.c_int), ("dense_immediate", ctypes.c_int)]
 
 
 class fvv_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in ("submitted", "completed", "superseded", "rejected", "failed",
                                                    "batches", "batched_views", "queued")] + \
                [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("dense_instants", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_size_t), ("dense_instants", ctypes.c_longlong),
+                ("age_p50_ms", ctypes.c_double), ("age_p99_ms", ctypes.c_double), ("stale_mean", ctypes.c_double),
+                ("stale_max", ctypes.c_longlong)]
 
 
 def _serve_sigs(L):
@@ -285,6 +301,7 @@ def _serve_sigs(L):
     L.fvv_serve_release.argtypes = [_P, ctypes.c_uint64]
     L.fvv_serve_stats_get.argtypes = [_P, ctypes.POINTER(fvv_serve_stats)]
     L.fvv_serve_destroy.argtypes = [_P]
+    L.fvv_serve_calibrate_fp8.argtypes = [_P, ctypes.c_int, _P, ctypes.c_int]
     L._serve_ready = True
     return L
 
@@ -311,6 +328,11 @@ def fvv_serve_create(weights, cfg: fvv_serve_cfg) -> int:
     s = _P()
     _check(L.fvv_serve_create(wp, n, ctypes.byref(cfg), ctypes.byref(s)))
     return s.value
+
+
+def fvv_serve_calibrate_fp8(s: int, res_id: int, frames, n_pairs: int):
+    """FP8 server: activation scales of every slot of one resolution (see fvv.h)."""
+    _check(_serve_sigs(lib()).fvv_serve_calibrate_fp8(s, res_id, _dev(frames), n_pairs))
 
 
 def fvv_serve_set_frames(s: int, instant: int, res_id: int, cams):

@@ -748,8 +748,12 @@ int fvv_calibrate_fp8(fvv_interp *h, const float *frames, int n_pairs, void *str
     h->calibrating = 1; // every layer in BF16, producers of FP8 inputs record max |output|
     FVV_CHECK_CUDA(cudaMemsetAsync(h->d_amax, 0, kNumLayers * sizeof(float), st));
     int rc = FVV_OK;
+    // all three t of every pair, in runs of at most max_views views: the scales do not
+    // depend on the handle's max_views
     for (int p = 0; p < n_pairs && rc == FVV_OK; ++p)
-        rc = fvv_interp_run(h, frames + 2 * p * img, frames + (2 * p + 1) * img, ts, nv, h->d_out, stream);
+        for (int t0 = 0; t0 < 3 && rc == FVV_OK; t0 += nv)
+            rc = fvv_interp_run(h, frames + 2 * p * img, frames + (2 * p + 1) * img, ts + t0, std::min(nv, 3 - t0),
+                                h->d_out, stream);
     h->calibrating = 0;
     if (rc != FVV_OK) return rc;
     float amax[kNumLayers];

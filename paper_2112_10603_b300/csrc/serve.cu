@@ -24,7 +24,10 @@
 //  * dense mode (dense_levels = n): per instant the fixed set t = k / 2^n of every
 //    pair is rendered once (batches of whole pairs) into one of two stores; requests
 //    snap t to that grid and are answered from the store of the newest frames, so
-//    the GPU work per instant does not depend on the number of users.
+//    the GPU work per instant does not depend on the number of users;  with
+//    dense_immediate every request is answered at once from the newest complete set,
+//    whatever instant it shows, and the server records how old that content is
+//    (time since its frames were set, and instants behind the newest frames).
 // With cfg.fake_ms_per_view > 0 nothing touches the GPU: a batch "runs" for
 // fake_ms_per_view x views milliseconds on the scheduler thread, so the queueing,
 // supersession, admission and latency logic can be tested on any machine.
@@ -81,6 +84,9 @@ struct Res {
     long long d_inst[2] = {-1, -1};  // complete instant held by each store
     int d_cur = -1;                  // store of the newest complete instant
     long long d_render = -1;         // instant being rendered (-1: none)
+    double frames_t = 0;             // when the newest frames were set
+    double d_time[2] = {0, 0};       // when the frames of each store's instant were set
+    double d_render_t = 0;           // when the frames being rendered were set
     int d_buf = 0;                   // store it renders into
     std::vector<const float *> d_cams;
     int d_next_pair = 0, d_pairs_done = 0;
@@ -106,6 +112,8 @@ struct fvv_server {
     int nd = 0;          // dense mode: views per pair (2^n - 1), 0 = on-demand mode
     int n_pairs = 0;
     std::vector<double> lat; // completed latencies (ms)
+    std::vector<double> age; // dense mode: age of the answered content (ms since its frames were set)
+    std::vector<long long> stale; // dense mode: instants between the answered set and the newest frames
     size_t dev_bytes = 0;
 };
 
@@ -160,6 +168,8 @@ void dense_answer(fvv_server *s, Request &r, double t) {
     r.t_done = t;
     s->st.completed++;
     s->lat.push_back(t - r.t_submit);
+    s->age.push_back(t - R.d_time[R.d_cur]);
+    s->stale.push_back(R.frames_id - R.d_inst[R.d_cur]);
 }
 
 struct RenderBatch {
@@ -182,6 +192,7 @@ void finish_render(RenderBatch *b) {
             R.d_render = -1; // retried by the scheduler on the newest frames
         } else if (b->instant == R.d_render && (R.d_pairs_done += b->n_pairs) == s->n_pairs) {
             R.d_inst[R.d_buf] = R.d_render;
+            R.d_time[R.d_buf] = R.d_render_t;
             R.d_cur = R.d_buf;
             R.d_render = -1;
             s->st.dense_instants++;
@@ -296,6 +307,7 @@ void scheduler(fvv_server *s) {
                     for (auto &sl : R.slots) idle = idle && !sl.busy;
                     if (idle) {
                         R.d_render = R.frames_id;
+                        R.d_render_t = R.frames_t;
                         R.d_buf = R.d_cur == 0 ? 1 : 0;
                         R.d_inst[R.d_buf] = -1;
                         R.d_cams = R.cams;
@@ -383,6 +395,9 @@ int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg 
         cfg->n_cams < 2 || cfg->pool_views < 1) {
         set_error("bad server configuration"); return FVV_EINVAL;
     }
+    if (cfg->precision != FVV_FP32 && cfg->precision != FVV_BF16 && cfg->precision != FVV_FP8) {
+        set_error("server precision must be FVV_FP32, FVV_BF16 or FVV_FP8"); return FVV_EINVAL;
+    }
     if (cfg->dense_levels < 0 || cfg->dense_levels > 8 ||
         (cfg->dense_levels > 0 && (1 << cfg->dense_levels) - 1 > cfg->max_batch)) {
         set_error("dense_levels must give 2^n - 1 <= max_batch views per pair"); return FVV_EINVAL;
@@ -455,6 +470,31 @@ int fvv_serve_create(const float *weights, size_t n_floats, const fvv_serve_cfg 
     return FVV_OK;
 }
 
+int fvv_serve_calibrate_fp8(fvv_server *s, int res_id, const float *frames, int n_pairs) {
+    clear_error();
+    if (!s || !frames || res_id < 0 || res_id >= (int)s->res.size() || n_pairs < 1) {
+        set_error("bad arguments"); return FVV_EINVAL;
+    }
+    if (s->cfg.precision != FVV_FP8) { set_error("the server does not run FP8"); return FVV_EINVAL; }
+    if (s->cfg.fake_ms_per_view > 0) return FVV_OK;
+    Res &R = s->res[res_id];
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &sl : R.slots)
+            if (sl.busy) { set_error("calibrate before the first frames of this resolution"); return FVV_EBUSY; }
+        for (auto &sl : R.slots) sl.busy = true; // the scheduler keeps off these slots meanwhile
+    }
+    int rc = FVV_OK;
+    for (auto &sl : R.slots)
+        if ((rc = fvv_calibrate_fp8(sl.h, frames, n_pairs, sl.st)) != FVV_OK) break;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &sl : R.slots) sl.busy = false;
+    }
+    s->cv.notify_all();
+    return rc;
+}
+
 int fvv_serve_set_frames(fvv_server *s, int64_t instant, int res_id, const float *const *cams_dev) {
     clear_error();
     if (!s || !cams_dev || res_id < 0 || res_id >= (int)s->res.size()) { set_error("bad arguments"); return FVV_EINVAL; }
@@ -462,6 +502,7 @@ int fvv_serve_set_frames(fvv_server *s, int64_t instant, int res_id, const float
     Res &R = s->res[res_id];
     R.cams.assign(cams_dev, cams_dev + s->cfg.n_cams);
     R.frames_id = instant;
+    R.frames_t = now_ms();
     s->cv.notify_all();
     return FVV_OK;
 }
@@ -500,8 +541,10 @@ int fvv_serve_submit(fvv_server *s, int user, int pair, float t, int res_id, uin
             r.t_done = r.t_submit;
             s->st.completed++;
             s->lat.push_back(0.0);
+            s->age.push_back(r.t_submit - R.frames_t);
+            s->stale.push_back(0);
             s->reqs[tk] = r;
-        } else if (R.d_cur >= 0 && R.d_inst[R.d_cur] == R.frames_id) {
+        } else if (R.d_cur >= 0 && (R.d_inst[R.d_cur] == R.frames_id || s->cfg.dense_immediate)) {
             s->reqs[tk] = r;
             dense_answer(s, s->reqs[tk], now_ms());
         } else {
@@ -586,6 +629,15 @@ int fvv_serve_stats_get(fvv_server *s, fvv_serve_stats *out) {
     out->p50_ms = pct(0.50);
     out->p99_ms = pct(0.99);
     out->max_ms = l.empty() ? 0.0 : l.back();
+    l = s->age;
+    std::sort(l.begin(), l.end());
+    out->age_p50_ms = pct(0.50);
+    out->age_p99_ms = pct(0.99);
+    double st_sum = 0;
+    long long st_max = 0;
+    for (long long v : s->stale) { st_sum += (double)v; st_max = std::max(st_max, v); }
+    out->stale_mean = s->stale.empty() ? 0.0 : st_sum / (double)s->stale.size();
+    out->stale_max = st_max;
     out->device_bytes = s->dev_bytes;
     out->queued = 0;
     for (auto &R : s->res) out->queued += (long long)R.queue.size() + (long long)R.d_waiting.size();

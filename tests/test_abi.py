@@ -70,3 +70,14 @@ def test_noalloc_source_allocates_nothing():
         assert banned not in code, banned
     assert re.search(r"static\s+__device__\s+__align__\(256\)\s+float\s+g_noalloc_w\[", code)
     assert "cudaGetSymbolAddress" in code
+
+
+def test_lap_loss_workspace_plan(lib):
+    """The loss's workspace (pyramid levels 2-5 + block sums) grows with the views and
+    is 0 for sizes the call rejects; no GPU needed."""
+    one = fvv.fvv_lap_loss_workspace(1, 1080, 1920)
+    seven = fvv.fvv_lap_loss_workspace(7, 1080, 1920)
+    # levels 2..5 hold about a third of a full-size image per view
+    assert 0.3 < one / (1080 * 1920 * 12) < 0.4
+    assert 6.9 < seven / one < 7.1
+    assert fvv.fvv_lap_loss_workspace(0, 8, 8) == 0 and fvv.fvv_lap_loss_workspace(1, 1, 8) == 0

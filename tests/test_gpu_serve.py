@@ -112,3 +112,47 @@ def test_dense_mode_views_match_alone():
             assert st["dense_instants"] == inst + 1 and st["failed"] == 0
     finally:
         fvv.fvv_serve_destroy(s)
+
+
+def test_dense_immediate_fp8_views_match_alone_and_oracle():
+    """FP8 dense server with immediate answers (3 levels, 7 views per pair): after the
+    first set has rendered, requests are answered at once; every answered view equals
+    the same view of an FP8 interpolator calibrated on the same frames (bit for bit),
+    and is held to the FP8 floor of the small-size tests against the oracle."""
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    h, w = 48, 80
+    frames_np = scene.rig(40, h, w, n_cams=3, max_disp=6.0)
+    cams = [torch.from_numpy(c).cuda() for c in frames_np]
+    cal = []
+    for sd in (100, 101):
+        cal += list(scene.stereo_pair(sd, h, w, 6.0))
+    cal_d = torch.from_numpy(np.stack(cal)).cuda()
+    cfg = fvv.fvv_serve_default_cfg(precision=fvv.FVV_FP8, n_res=1, res_h=[h], res_w=[w], n_cams=3,
+                                    slots_per_res=2, max_batch=14, dense_levels=3, dense_immediate=1)
+    s = fvv.fvv_serve_create(blob(), cfg)
+    alone = fvv.Interpolator(blob(), h, w, precision=fvv.FVV_FP8, max_views=1)
+    fvv.fvv_calibrate_fp8(alone.h, cal_d, 2)
+    try:
+        fvv.fvv_serve_calibrate_fp8(s, 0, cal_d, 2)
+        fvv.fvv_serve_set_frames(s, 0, 0, cams)
+        t0 = time.time()
+        while fvv.fvv_serve_stats_get(s)["dense_instants"] < 1:
+            assert time.time() - t0 < 60
+            time.sleep(0.002)
+        for u, (p, t) in enumerate([(0, 0.3), (1, 0.5), (0, 0.88), (1, 0.12)]):
+            tk = fvv.fvv_serve_submit(s, u, p, t, 0)
+            st, ptr, lat = fvv.fvv_serve_poll(s, tk)
+            assert st == 0                                   # answered at submit
+            got = _fetch(ptr, (h, w, 3))
+            k = min(8, max(0, round(t * 8)))
+            ref = alone.run(cams[p], cams[p + 1], [k / 8]).cpu().numpy()[0]
+            np.testing.assert_array_equal(got, ref)
+            ref64 = oracle.vinet_forward(blob(), frames_np[p], frames_np[p + 1], k / 8)
+            assert psnr(got, ref64) >= 30.0, (p, t, psnr(got, ref64))
+            fvv.fvv_serve_release(s, tk)
+        st = fvv.fvv_serve_stats_get(s)
+        assert st["failed"] == 0 and st["stale_max"] == 0
+    finally:
+        fvv.fvv_serve_destroy(s)

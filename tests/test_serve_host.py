@@ -161,3 +161,39 @@ def test_dense_mode_needs_whole_pairs_per_batch():
     with pytest.raises(fvv.FvvError) as e:
         fvv.fvv_serve_create(None, cfg)
     assert e.value.code == fvv.FVV_EINVAL
+
+
+def test_dense_immediate_answers_from_newest_set_with_staleness():
+    """dense_immediate: while the newest frames render, requests are answered at once
+    from the newest complete set (the older instant), and the stats count how stale
+    that content is; once the new set completes, answers come from it (staleness 0)."""
+    s = _server(slots_per_res=2, max_batch=6, dense_levels=2, fake=10.0, dense_immediate=1)
+    view_bytes = 64 * 64 * 3 * 4
+    cams = [0x1000 * (i + 1) for i in range(5)]
+    try:
+        fvv.fvv_serve_set_frames(s, 0, 0, cams)
+        tk = fvv.fvv_serve_submit(s, 1, 0, 0.5, 0)       # no set yet: waits for the first one
+        _wait(s, tk)
+        assert fvv.fvv_serve_stats_get(s)["dense_instants"] == 1
+        fvv.fvv_serve_set_frames(s, 1, 0, cams)           # renders for ~2 x 60 ms
+        time.sleep(0.01)
+        t0 = time.time()
+        tks = [fvv.fvv_serve_submit(s, 10 + u, 1, 0.5, 0) for u in range(8)]
+        for tk in tks:
+            st, ptr, lat = fvv.fvv_serve_poll(s, tk)      # answered at submit: no waiting
+            assert st == 0 and lat < 5.0
+            assert ptr == (1 << 40) + (1 * 3 + 1) * view_bytes   # the first store (instant 0)
+        assert time.time() - t0 < 0.05
+        st = fvv.fvv_serve_stats_get(s)
+        assert st["stale_max"] == 1 and st["dense_instants"] == 1
+        t1 = time.time()
+        while fvv.fvv_serve_stats_get(s)["dense_instants"] < 2:
+            assert time.time() - t1 < 5
+            time.sleep(0.005)
+        tk = fvv.fvv_serve_submit(s, 50, 1, 0.5, 0)
+        st, ptr, lat = fvv.fvv_serve_poll(s, tk)
+        assert st == 0 and ptr == (2 << 40) + (1 * 3 + 1) * view_bytes
+        st = fvv.fvv_serve_stats_get(s)
+        assert 0 < st["stale_mean"] < 1 and st["age_p99_ms"] > 0
+    finally:
+        fvv.fvv_serve_destroy(s)
