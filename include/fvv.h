@@ -64,7 +64,11 @@ typedef struct {
     int max_views; /* views per run call the workspace is sized for (>= 1) */
     int max_cams;  /* cameras per batched call (>= 2) */
     int graphs;    /* 1: each run replays a CUDA graph captured on first use for its
-                      (cameras, views) count; 0: launch kernels directly */
+                      view-count bucket (the next power of two of the call's views, at
+                      most max_views; launches sized for max_cams cameras): the kernels
+                      read the call's view and camera counts from device memory and
+                      skip the rest of their grid, so any mix of counts replays one of
+                      at most 1 + log2(max_views) graphs; 0: launch kernels directly */
 } fvv_opts;
 
 typedef struct fvv_interp fvv_interp;
@@ -130,6 +134,9 @@ size_t fvv_interp_device_bytes(const fvv_interp *h);
 
 /* Number of kernel launches the last run call issued. */
 int fvv_interp_last_launches(const fvv_interp *h);
+
+/* Number of CUDA graphs the handle has captured so far (opts.graphs = 1). */
+long long fvv_interp_graph_captures(const fvv_interp *h);
 
 /* Copy an intermediate of view `view` from the last run into `dst` (HOST,
  * float32), synchronising the device first.  which: 0, 1, 2 = stage s flows and

@@ -61,6 +61,8 @@ def lib():
         L.fvv_interp_device_bytes.argtypes = [_P]
         L.fvv_interp_device_bytes.restype = ctypes.c_size_t
         L.fvv_interp_last_launches.argtypes = [_P]
+        L.fvv_interp_graph_captures.argtypes = [_P]
+        L.fvv_interp_graph_captures.restype = ctypes.c_longlong
         L.fvv_interp_peek.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]
         L.fvv_interp_layer.argtypes = [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P] + [ctypes.c_int] * 3 + [_P]
         L.fvv_interp_status.argtypes = [_P]
@@ -187,6 +189,10 @@ def fvv_interp_device_bytes(h: int) -> int:
 
 def fvv_interp_last_launches(h: int) -> int:
     return lib().fvv_interp_last_launches(h)
+
+
+def fvv_interp_graph_captures(h: int) -> int:
+    return int(lib().fvv_interp_graph_captures(h))
 
 
 def fvv_interp_peek(h: int, which: int, view: int, shape):

@@ -51,6 +51,7 @@ struct ConvArgs {
     int N, H, W;        // input images and size
     int Ci, Co, Ho, Wo; // Ho, Wo = output size
     int kind, stride, relu, circ;
+    const int *n_dev;   // device count of images actually run (graph replay of a size bucket), or NULL
 };
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

@@ -75,12 +75,13 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(ConvArgs a) {
     const bool convt = a.kind == K_CONVT;
     // GEMM rows: conv -> output pixels; convT -> input-grid pixels of this phase
     const int GH = convt ? a.H : a.Ho, GW = convt ? a.W : a.Wo;
-    const int Mtot = a.N * GH * GW;
+    const int Mtot = dev_count(a.n_dev, a.N) * GH * GW;
     const int taps = convt ? 4 : 9;
     const int K = taps * a.Ci;
     if (convt) wp += (size_t)phase * K * a.Co;
 
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    if (m0 >= Mtot) return; // the whole block lies beyond the images run (size-bucket launch)
 
     float acc[4][4];
 #pragma unroll
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) conv_c3_kernel(ConvArgs a) {
     if (threadIdx.x < 16) bs[threadIdx.x] = a.bias[threadIdx.x];
     __syncthreads();
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)a.N * a.Ho * a.Wo) return;
+    if (idx >= (long long)dev_count(a.n_dev, a.N) * a.Ho * a.Wo) return;
     int ox = idx % a.Wo;
     long long r = idx / a.Wo;
     int oy = r % a.Ho, n = r / a.Ho;

@@ -68,6 +68,7 @@ struct TcParams {
     int tma_store;          // epilogue stages each warp's 32 rows in shared memory, TMA stores them
     int kxf;                // column taps folded into N: tiles of kKxfTile output pixels of one row
     int wcopies;            // per-tap stride-2 path: weight copies (CTA b reads copy b % wcopies)
+    const int *n_dev;       // device count of images actually run (graph replay of a size bucket), or NULL
     long long stall_cycles; // fault injection (tests): > 0 makes the MMA warp wait on a barrier
                             // nothing signals, for at most this many cycles, then abort
 };
@@ -112,8 +113,9 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
     }
 }
 
-__device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase, int &n, int &y0, int &x0) {
-    int per_phase = p.n_img * p.tiles_y * p.tiles_x;
+__device__ __forceinline__ void tile_coords(const TcParams &p, int n_img, int t, int &phase, int &n, int &y0,
+                                            int &x0) {
+    int per_phase = n_img * p.tiles_y * p.tiles_x;
     phase = t / per_phase;
     int r = t - phase * per_phase;
     int tx = r % p.tiles_x;
@@ -323,6 +325,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     ptx::tc_fence_after();
     const uint32_t tmem = bars->tmem_base;
     const int kblocks = p.taps * p.nck;
+    // images actually run: a launch captured for a size bucket reads the call's count
+    const int n_img = p.n_dev ? min(__ldg(p.n_dev), p.n_img) : p.n_img;
+    const int num_tiles = p.n_dev ? n_img * p.tiles_y * p.tiles_x * (p.mode == MODE_T ? 4 : 1) : p.num_tiles;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -336,9 +341,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t ph_bit = 0;
             long long issued = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t, ph, n, y0, x0);
+                tile_coords(p, n_img, t, ph, n, y0, x0);
                 for (int ky = 0; ky < 3; ++ky) {
                     if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
                     const uint32_t fs = ptx::smem_u32(&bars->full[s]);
@@ -380,9 +385,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t ph_bit = 0;
             long long issued = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t, ph, n, y0, x0);
+                tile_coords(p, n_img, t, ph, n, y0, x0);
                 for (int ky = 0; ky < 3 && !stop; ++ky)
                     for (int c = 0; c < p.nck; ++c) {
                         if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
@@ -421,9 +426,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t pa = 0, pb = 0;
             long long issued_a = 0, issued_b = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort && !stop; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t, ph, n, y0, x0);
+                tile_coords(p, n_img, t, ph, n, y0, x0);
                 // boxes in K order (ky, channel block)
                 const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && !stop; ++grp) {
@@ -466,9 +471,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int stage = 0;
             uint32_t phase_bit = 0;
             long long issued = 0;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, t, ph, n, y0, x0);
+                tile_coords(p, n_img, t, ph, n, y0, x0);
                 for (int kb = 0; kb < kblocks; ++kb) {
                     if (!wait_bar(ptx::smem_u32(&bars->empty[stage]), phase_bit ^ 1, abort, p.err, 1)) break;
                     int tap = kb / p.nck, c0 = (kb - tap * p.nck) * CK;
@@ -530,7 +535,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool ok = wait_bar(ptx::smem_u32(&bars->full[STAGES]), 0, abort, p.err, 3); // resident weights
             ptx::tc_fence_after();
             const uint32_t bw = ptx::smem_u32(sB);
-            for (int t = blockIdx.x; ok && t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; ok && t < num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem + acc * BN;
@@ -573,7 +578,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // GRP == 2: the resident weight slices (one channel block: group g = row tap ky)
             const bool wok = GRP != 2 || wait_bar(ptx::smem_u32(&bars->full[STAGES]), 0, abort, p.err, 3);
             ptx::tc_fence_after();
-            for (int t = blockIdx.x; wok && t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; wok && t < num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem + acc * (MT * BN);
@@ -631,7 +636,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem + acc * (MT * BN);
@@ -684,7 +689,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
                 if (!wait_bar(ptx::smem_u32(&bars->tmem_empty[acc]), acc_phase ^ 1, abort, p.err, 2)) break;
                 ptx::tc_fence_after();
                 uint32_t d = tmem + acc * (MT * BN);
@@ -737,9 +742,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         // fused network output (N = 16 tiles): the cropped output buffer
         float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
-        for (int t = blockIdx.x; t < p.num_tiles && !*abort; t += gridDim.x) {
+        for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
-            tile_coords(p, t, ph, n, y0, x0);
+            tile_coords(p, n_img, t, ph, n, y0, x0);
             int gy = y0 + dy, gx = x0 + dx;
             bool valid = gy < p.gh && gx < p.gw;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
@@ -1672,6 +1677,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.bias = h->bias + h->b_off[li];
     p.err = h->d_err;
     p.stall_cycles = h->stall_now;
+    p.n_dev = count_word(h, li);
     if (epi) {
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them

@@ -138,6 +138,7 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
     a.bias = h->bias + h->b_off[li];
     a.N = N; a.H = Hin; a.W = Win; a.Ci = L.ci; a.Co = L.co;
     a.kind = L.kind; a.stride = L.stride; a.relu = L.relu; a.circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
+    a.n_dev = count_word(h, li);
     if (L.kind == K_CONV) { a.Ho = (Hin - 1) / L.stride + 1; a.Wo = (Win - 1) / L.stride + 1; }
     else { a.Ho = 2 * Hin; a.Wo = 2 * Win; }
     if (li == kCtx) return launch_conv_c3(a, is_bf16(h) && !out_f32, st);
@@ -148,14 +149,17 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     const int Hp = h->Hp, Wp = h->Wp, circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
     const bool b16 = is_bf16(h);
     const int cx0 = b16 ? 16 : 7, cx1 = b16 ? 32 : 18, cu0 = b16 ? 16 : 6;
-    ViewTab vt{h->d_cam_l, h->d_cam_r, h->d_t};
+    // while a size-bucket graph is captured, every kernel reads the call's counts
+    const int *nv_dev = h->counts_live ? h->d_cnt : nullptr, *nc_dev = h->counts_live ? h->d_cnt + 1 : nullptr;
+    ViewTab vt{h->d_cam_l, h->d_cam_r, h->d_t, nv_dev};
     T *xb = (T *)h->xb, *ta = (T *)h->ta, *ma = (T *)h->ma, *mb = (T *)h->mb;
     T *U[5];
     for (int k = 0; k < 5; ++k) U[k] = (T *)h->u[k];
 
     // a0: pyramid of every camera; a1: ContextNet, batched over cameras.  Skipped
     // when the caller (the server) knows the frames are those of the handle's last run.
-    if (!h->skip_cams) FVV_TRY(launch_prep_cams(h->d_cams, n_cams, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
+    if (!h->skip_cams)
+        FVV_TRY(launch_prep_cams(h->d_cams, n_cams, nc_dev, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
     if (!h->skip_cams) {
         int hh = Hp, ww = Wp;
         const void *cur = h->img0; // FP32 frame: the 3-channel first layer runs on the SIMT kernel
@@ -193,7 +197,7 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st, &e));
         } else {
             FVV_TRY(conv(h, base + 9, ta, 128, 0, nv, hs / 2, ws / 2, h->fm[s], 5, 0, true, st));
-            if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, hs, ws, circ, st));
+            if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, nv_dev, hs, ws, circ, st));
         }
     }
     // a5: final warp + blend
@@ -239,7 +243,7 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st, &e));
         } else {
             FVV_TRY(conv(h, kRef + 12, ta, 16, 0, nv, Hp, Wp, h->z, 3, 0, true, st));
-            FVV_TRY(launch_output(h->ib, h->z, 3, nv, Hp, Wp, h->H, h->W, h->d_outp, st));
+            FVV_TRY(launch_output(h->ib, h->z, 3, nv, nv_dev, Hp, Wp, h->H, h->W, h->d_outp, st));
         }
     }
     return FVV_OK;
@@ -311,6 +315,7 @@ static int create_impl(fvv_interp *h, const float *blob) {
     FVV_TRY(dalloc_t(h, &h->d_cams, C * sizeof(float *)));
     FVV_TRY(dalloc_t(h, &h->d_err, 64));
     FVV_TRY(dalloc_t(h, &h->d_outp, sizeof(float *)));
+    FVV_TRY(dalloc_t(h, &h->d_cnt, 2 * sizeof(int)));
     FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, 64));
     FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + (C + 1) * sizeof(float *) + 64));
@@ -330,11 +335,14 @@ static int upload_tables(fvv_interp *h, const float *const *cams, int n_cams, co
     memcpy(s + V * 12, cams, n_cams * sizeof(float *));
     char *so = s + V * 12 + h->o.max_cams * sizeof(float *);
     memcpy(so, &out, sizeof(float *));
+    const int counts[2] = {nv, n_cams};
+    memcpy(so + sizeof(float *), counts, sizeof counts);
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_l, s, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cam_r, s + V * 4, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_t, s + V * 8, nv * 4, cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cams, s + V * 12, n_cams * sizeof(float *), cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_outp, so, sizeof(float *), cudaMemcpyHostToDevice, st));
+    FVV_CHECK_CUDA(cudaMemcpyAsync(h->d_cnt, so + sizeof(float *), 2 * sizeof(int), cudaMemcpyHostToDevice, st));
     FVV_CHECK_CUDA(cudaEventRecord(h->stage_done, st));
     return FVV_OK;
 }
@@ -345,21 +353,33 @@ static void drop_graphs(fvv_interp *h) {
 }
 
 // Run the forward for (n_cams, nv) after the tables are uploaded: direct launches
-// while profiling or with graphs off, else replay the graph captured for that count
-// (captured on first use; every buffer it touches is fixed per handle and the
-// per-call data -- view table, camera and output pointers -- is read from device slots).
+// while profiling or with graphs off, else replay a graph (captured on first use; every
+// buffer it touches is fixed per handle and the per-call data -- view table, camera and
+// output pointers, the view and camera counts -- is read from device slots).  A graph
+// is captured for a size bucket, not for one count: launches shaped for the next power
+// of two of views (at most max_views) and for max_cams cameras, every kernel running
+// only the uploaded counts (the rest of its grid exits at once).  So any mix of view
+// counts replays one of at most 1 + log2(max_views) graphs (twice that with the
+// server's cached-frame runs) instead of capturing one per distinct count.
 static int dispatch_forward(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
     if (h->o.precision == FVV_FP8 && !h->fp8_ready && !h->calibrating) {
         set_error("FP8 handle: call fvv_calibrate_fp8 before running");
         return FVV_EINVAL;
     }
     if (!h->o.graphs || h->profiling || h->calibrating) return interp_forward(h, n_cams, nv, st);
-    long long key = ((long long)n_cams * 65536 + nv) * 2 + (h->skip_cams ? 1 : 0);
+    int vb = 1;
+    while (vb < nv) vb <<= 1;
+    if (vb > h->o.max_views) vb = h->o.max_views;
+    const int cb = h->o.max_cams;
+    long long key = ((long long)cb * 65536 + vb) * 2 + (h->skip_cams ? 1 : 0);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
         FVV_CHECK_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-        int rc = interp_forward(h, n_cams, nv, h->cap_stream);
+        h->counts_live = true;
+        int rc = interp_forward(h, cb, vb, h->cap_stream);
+        h->counts_live = false;
+        ++h->graph_captures;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc != FVV_OK) { if (g) cudaGraphDestroy(g); return rc; }
         FVV_CHECK_CUDA(e);
@@ -894,6 +914,7 @@ int fvv_interp_autotune(fvv_interp *h, int n_views, const char *cache_path) {
 
 size_t fvv_interp_device_bytes(const fvv_interp *h) { return h ? h->dev_bytes : 0; }
 int fvv_interp_last_launches(const fvv_interp *h) { return h ? h->last_launches : 0; }
+long long fvv_interp_graph_captures(const fvv_interp *h) { return h ? h->graph_captures : 0; }
 
 void fvv_interp_destroy(fvv_interp *h) {
     if (!h) return;

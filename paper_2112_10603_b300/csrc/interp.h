@@ -97,9 +97,13 @@ struct fvv_interp {
     std::vector<cudaEvent_t> ev_pool;
     // output pointer slot read by the last kernel (so a captured graph serves any buffer)
     float **d_outp = nullptr;
-    // CUDA graphs, one per (cameras, views) count, captured on cap_stream
+    // CUDA graphs, one per view-count bucket (and cached-frames flag), captured on cap_stream;
+    // d_cnt = {views, cameras} of the current call, read by every kernel of a bucket graph
     struct Graph { cudaGraphExec_t exec; int launches; };
     std::map<long long, Graph> graphs;
+    int *d_cnt = nullptr;
+    bool counts_live = false; // set while a bucket graph is captured
+    long long graph_captures = 0;
     cudaStream_t cap_stream = nullptr;
     // tile rectangle per layer: log2 of the tile width (-1: fewest-tiles default);
     // tile_force >= 0 overrides every layer (used while autotuning)
@@ -135,5 +139,11 @@ bool tc_kxf_layer(int layer);   // column taps folded into N (tiles of 120 pixel
 // transposed, all phases); their producers are the layer before (c0 .. t0) and write
 // E4M3 codes.
 inline bool fp8_layer(int li) { return li < kCtx && li % 10 >= 1; }
+// Device count word a conv layer's launch reads while a size-bucket graph is captured:
+// cameras for ContextNet's layers, views for every other layer; NULL otherwise.
+inline const int *count_word(const fvv_interp *h, int li) {
+    if (!h->counts_live) return nullptr;
+    return h->d_cnt + (li >= kCtx && li < kCtx + 8 ? 1 : 0);
+}
 inline bool feeds_fp8(int li) { return li < kCtx && li % 10 <= 8; }
 } // namespace fvv

@@ -61,8 +61,9 @@ __device__ __forceinline__ float3 bilerp_rgb(const float4 *img, const Taps &t) {
 // ---------------------------------------------------------------------------
 // a0: zero-pad each camera frame to Hp x Wp and build its 1/2 box level.
 // One thread per 2x2 block (= one pixel of the 1/2 level).
-__global__ void prep_cams_kernel(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp,
-                                 float4 *img0, float4 *img1) {
+__global__ void prep_cams_kernel(const float *const *cams, int n_cams, const int *ncam_dev, int H, int W, int Hp,
+                                 int Wp, float4 *img0, float4 *img1) {
+    n_cams = dev_count(ncam_dev, n_cams);
     int h2 = Hp / 2, w2 = Wp / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n_cams * h2 * w2) return;
@@ -93,7 +94,9 @@ __global__ void prep_cams_kernel(const float *const *cams, int n_cams, int H, in
 }
 
 // a0: the 1/4 level as the 2x2 box average of the 1/2 level (= the 4x4 box).
-__global__ void box_quarter_kernel(const float4 *img1, int n_cams, int h2, int w2, float4 *img2) {
+__global__ void box_quarter_kernel(const float4 *img1, int n_cams, const int *ncam_dev, int h2, int w2,
+                                   float4 *img2) {
+    n_cams = dev_count(ncam_dev, n_cams);
     int h4 = h2 / 2, w4 = w2 / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n_cams * h4 * w4) return;
@@ -110,6 +113,7 @@ __global__ void box_quarter_kernel(const float4 *img1, int n_cams, int h2, int w
 // a2 input: [I_l/4, I_r/4, t] (7 channels, zero-padded to cs).
 template <typename T>
 __global__ void vib0_input_kernel(const float4 *img2, const ViewTab vt, int nv, int h, int w, T *x, int cs) {
+    nv = dev_count(vt.n, nv);
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)h * w;
     if (idx >= (long long)nv * P) return;
@@ -137,6 +141,7 @@ __device__ __forceinline__ bool tile_pixel(int h, int w, int &X, int &Y) {
 template <typename T>
 __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const ViewTab vt, int nv,
                                    int h, int w, int circ, T *x, int cs) {
+    nv = dev_count(vt.n, nv);
     const long long P = (long long)h * w;
     int X, Y;
     if (!tile_pixel(h, w, X, Y)) return;
@@ -166,7 +171,8 @@ __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const V
 }
 
 // Eq. 2: F^s, M^s = up(F^{s-1}) x2, up(M^{s-1}) + Res^s  (in place on res).
-__global__ void residual_kernel(const float *FMp, float *res, int nv, int h, int w, int circ) {
+__global__ void residual_kernel(const float *FMp, float *res, int nv, const int *nv_dev, int h, int w, int circ) {
+    nv = dev_count(nv_dev, nv);
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)h * w;
     if (idx >= (long long)nv * P) return;
@@ -186,6 +192,7 @@ __global__ void residual_kernel(const float *FMp, float *res, int nv, int h, int
 template <typename T>
 __global__ void final_blend_kernel(const float4 *__restrict__ img0, const float *__restrict__ FM, const ViewTab vt,
                                    int nv, int h, int w, int circ, T *__restrict__ u0, int cs, float *__restrict__ ib) {
+    nv = dev_count(vt.n, nv);
     const long long P = (long long)h * w;
     int X, Y;
     if (!tile_pixel(h, w, X, Y)) return;
@@ -256,6 +263,7 @@ template <typename T>
 __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C,
                                 const ViewTab vt, int nv, int h, int w, int circ,
                                 T *dst, int dst_cs, int off_l, int off_r) {
+    nv = dev_count(vt.n, nv);
     const int groups = C / 8;
     const long long P = (long long)h * w;
     const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,8 +300,9 @@ __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, con
 }
 
 // a8: out = clamp(I_blend + 2 sigmoid(z) - 1, 0, 1), cropped to H x W.
-__global__ void output_kernel(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp,
+__global__ void output_kernel(const float *ib, const float *z, int z_cs, int nv, const int *nv_dev, int Hp, int Wp,
                               int H, int W, float *const *outp) {
+    nv = dev_count(nv_dev, nv);
     float *out = *outp;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long P = (long long)H * W;
@@ -318,13 +327,13 @@ inline unsigned tile_blocks(int h, int w) { return (unsigned)(((w + 31) / 32) * 
 #define FVV_LAUNCH_CHECK() \
     do { count_launch(); FVV_CHECK_CUDA(cudaGetLastError()); } while (0)
 
-int launch_prep_cams(const float *const *cams, int n_cams, int H, int W, int Hp, int Wp, float4 *img0,
-                     float4 *img1, float4 *img2, cudaStream_t st) {
+int launch_prep_cams(const float *const *cams, int n_cams, const int *ncam_dev, int H, int W, int Hp, int Wp,
+                     float4 *img0, float4 *img1, float4 *img2, cudaStream_t st) {
     long long n = (long long)n_cams * (Hp / 2) * (Wp / 2);
-    prep_cams_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cams, n_cams, H, W, Hp, Wp, img0, img1);
+    prep_cams_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cams, n_cams, ncam_dev, H, W, Hp, Wp, img0, img1);
     FVV_LAUNCH_CHECK();
     n = (long long)n_cams * (Hp / 4) * (Wp / 4);
-    box_quarter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(img1, n_cams, Hp / 2, Wp / 2, img2);
+    box_quarter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(img1, n_cams, ncam_dev, Hp / 2, Wp / 2, img2);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
@@ -345,9 +354,10 @@ int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, 
     return FVV_OK;
 }
 
-int launch_residual(const float *FMp, float *res, int nv, int h, int w, int circ, cudaStream_t st) {
+int launch_residual(const float *FMp, float *res, int nv, const int *nv_dev, int h, int w, int circ,
+                    cudaStream_t st) {
     long long n = (long long)nv * h * w;
-    residual_kernel<<<blocks_for(n, 256), 256, 0, st>>>(FMp, res, nv, h, w, circ);
+    residual_kernel<<<blocks_for(n, 256), 256, 0, st>>>(FMp, res, nv, nv_dev, h, w, circ);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
@@ -370,10 +380,10 @@ int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, i
     return FVV_OK;
 }
 
-int launch_output(const float *ib, const float *z, int z_cs, int nv, int Hp, int Wp, int H, int W, float *const *outp,
-                  cudaStream_t st) {
+int launch_output(const float *ib, const float *z, int z_cs, int nv, const int *nv_dev, int Hp, int Wp, int H, int W,
+                  float *const *outp, cudaStream_t st) {
     long long n = (long long)nv * H * W;
-    output_kernel<<<blocks_for(n, 256), 256, 0, st>>>(ib, z, z_cs, nv, Hp, Wp, H, W, outp);
+    output_kernel<<<blocks_for(n, 256), 256, 0, st>>>(ib, z, z_cs, nv, nv_dev, Hp, Wp, H, W, outp);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }

@@ -68,6 +68,10 @@ class Interpolator:
     def last_launches(self) -> int:
         return L.fvv_interp_last_launches(self.h)
 
+    @property
+    def graph_captures(self) -> int:
+        return L.fvv_interp_graph_captures(self.h)
+
     def close(self):
         if self.h:
             L.fvv_interp_destroy(self.h)

@@ -108,3 +108,32 @@ def test_rig_instant_matches_oracle(torch_cuda):
             else:
                 assert psnr(out[v], ref) >= 45.0, (v, psnr(out[v], ref))
         it.close()
+
+
+@pytest.mark.parametrize("precision", [fvv.FVV_FP32, fvv.FVV_BF16])
+def test_bucket_graphs_replay_any_view_mix(torch_cuda, precision):
+    """Graphs are captured per view-count bucket (powers of two up to max_views), the
+    kernels reading the call's counts from device memory: 24 rig instants with random
+    per-pair counts (4..16 views) and single-pair calls of 1..16 views replay at most
+    five graphs, and every output equals direct launches bit for bit."""
+    torch = torch_cuda
+    H, W = 48, 80
+    cams = [torch.from_numpy(c).cuda() for c in scene.rig(16, H, W, n_cams=5, max_disp=6.0)]
+    g = fvv.Interpolator(blob(), H, W, precision=precision, max_views=16, max_cams=5, graphs=1)
+    d = fvv.Interpolator(blob(), H, W, precision=precision, max_views=16, max_cams=5, graphs=0)
+    rng = np.random.default_rng(16)
+    for _ in range(24):
+        counts = rng.integers(1, 5, 4)
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        ts = np.concatenate([np.sort(rng.uniform(0, 1, c)) for c in counts]).astype(np.float32)
+        a = g.run_batch(cams, [0, 1, 2, 3], offs, ts).cpu().numpy()
+        b = d.run_batch(cams, [0, 1, 2, 3], offs, ts).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+    for nv in (1, 3, 2, 16, 5, 9):
+        ts = rng.uniform(0, 1, nv).astype(np.float32)
+        a = g.run(cams[1], cams[2], ts).cpu().numpy()
+        b = d.run(cams[1], cams[2], ts).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+    fvv.fvv_interp_status(g.h)
+    assert g.graph_captures <= 5, g.graph_captures      # buckets 1, 2, 4, 8, 16
+    assert d.graph_captures == 0
