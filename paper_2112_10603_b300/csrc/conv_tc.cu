@@ -69,6 +69,8 @@ struct TcParams {
     int kxf;                // column taps folded into N: tiles of kKxfTile output pixels of one row
     int wcopies;            // per-tap stride-2 path: weight copies (CTA b reads copy b % wcopies)
     const int *n_dev;       // device count of images actually run (graph replay of a size bucket), or NULL
+    int ipad;               // circular mode: the input carries a wrapped border of ipad pixels (A coordinates
+                            // shift by ipad pixels, ipad / 2 pixel pairs on the stride-2 maps); 0 otherwise
     long long stall_cycles; // fault injection (tests): > 0 makes the MMA warp wait on a barrier
                             // nothing signals, for at most this many cycles, then abort
 };
@@ -325,6 +327,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     ptx::tc_fence_after();
     const uint32_t tmem = bars->tmem_base;
     const int kblocks = p.taps * p.nck;
+    const int ip = p.ipad, pp = p.ipad >> 1; // circular mode: A coordinates in the wrapped-border input
     // images actually run: a launch captured for a size bucket reads the call's count
     const int n_img = p.n_dev ? min(__ldg(p.n_dev), p.n_img) : p.n_img;
     const int num_tiles = p.n_dev ? n_img * p.tiles_y * p.tiles_x * (p.mode == MODE_T ? 4 : 1) : p.num_tiles;
@@ -350,8 +353,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ptx::mbar_arrive_expect_tx(fs, A_BYTES);
                     // input row 2 y0 + ky - 1 = (row pair, parity) (y0 - 1, 1), (y0, 0), (y0, 1);
                     // pairs x0 - 1 .. x0 + 127 (both pixels of each)
-                    ptx::tma_load_5d(ptx::smem_u32(sA + s * A_STRIDE), &tmA, fs, 0, x0 - 1, ky != 1 ? 1 : 0,
-                                     y0 - (ky == 0 ? 1 : 0), n);
+                    ptx::tma_load_5d(ptx::smem_u32(sA + s * A_STRIDE), &tmA, fs, 0, x0 - 1 + pp, ky != 1 ? 1 : 0,
+                                     y0 - (ky == 0 ? 1 : 0) + pp, n);
                     ++issued;
                     if (++s == STAGES) { s = 0; ph_bit ^= 1; }
                 }
@@ -398,9 +401,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
                                 ptx::tma_load_4d(base + q * 32 * ROW_BYTES, &tmA, fs, p.in_coff + c * CK,
-                                                 x0 - 1 + 30 * q, y0 + ky - 1, n);
+                                                 x0 - 1 + 30 * q + ip, y0 + ky - 1 + ip, n);
                         } else {
-                            ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1, y0 + ky - 1, n);
+                            ptx::tma_load_4d(base, &tmA, fs, p.in_coff + c * CK, x0 - 1 + ip, y0 + ky - 1 + ip, n);
                         }
                         if (GRP == 1)
                             ptx::tma_load_3d(base + A_STRIDE, &tmB, fs, c * CK, 0, ky * 3); // taps ky*3 .. ky*3+2
@@ -436,8 +439,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
                         uint32_t fa = ptx::smem_u32(&bars->full[sa]);
                         ptx::mbar_arrive_expect_tx(fa, A_BYTES);
-                        ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1,
-                                         y0 + ky - 1, n);
+                        ptx::tma_load_4d(ptx::smem_u32(sA + sa * A_STRIDE), &tmA, fa, p.in_coff + c * CK, x0 - 1 + ip,
+                                         y0 + ky - 1 + ip, n);
                         ++issued_a;
                         if (++sa == STAGES) { sa = 0; pa ^= 1; }
                         for (int kx = 0; kx < NB; ++kx) {
@@ -485,13 +488,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         const int ky = kb / (3 * p.nck), r = kb - ky * 3 * p.nck, kx = r % 3;
                         c0 = (r / 3) * CK;
                         tap = ky * 3 + kx;
-                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1, y0 + ky - 1, n);
+                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1 + ip, y0 + ky - 1 + ip, n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, tap);
                     } else if (p.mode == MODE_S2) {
                         int ky = tap / 3, kx = tap - 3 * (tap / 3);
                         int half = kx == 1 ? 0 : 1, rpar = ky == 1 ? 0 : 1;
-                        ptx::tma_load_5d(da, &tmA, fb, half * p.in_cs + p.in_coff + c0, x0 - (kx == 0 ? 1 : 0), rpar,
-                                         y0 - (ky == 0 ? 1 : 0), n);
+                        ptx::tma_load_5d(da, &tmA, fb, half * p.in_cs + p.in_coff + c0, x0 - (kx == 0 ? 1 : 0) + pp,
+                                         rpar, y0 - (ky == 0 ? 1 : 0) + pp, n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0,
                                          tap + (p.wcopies > 1 ? 9 * (int)(blockIdx.x % (unsigned)p.wcopies) : 0));
                     } else {
@@ -500,7 +503,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         c0 = (kb >> 2) * CK;
                         int py = ph >> 1, px = ph & 1, ty = tap >> 1, tx = tap & 1;
                         int dy = py == 0 ? -ty : 1 - ty, dx = px == 0 ? -tx : 1 - tx;
-                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + dx, y0 + dy, n);
+                        ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + dx + ip, y0 + dy + ip, n);
                         ptx::tma_load_3d(db, &tmB, fb, c0, 0, ph * 4 + tap);
                     }
                     ++issued;
@@ -1436,10 +1439,6 @@ int fold_column_taps(fvv_interp *h, TcWeights &tw, const std::vector<T> &pk, int
 
 int tc_prepare(fvv_interp *h, const float *blob) {
     FVV_TRY(get_encoder());
-    if (h->o.pad_mode != FVV_PAD_ZERO) {
-        set_error("the tensor-core path supports zero padding only (circular mode runs in FP32)");
-        return FVV_EINVAL;
-    }
     size_t off = 0;
     struct Fold { int li; std::vector<bf16> pk; int cop, cip, G, ck; };
     std::vector<Fold> folds;
@@ -1623,6 +1622,21 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
         set_error("layer %s: input slice (cs %d, off %d, %d ch) not TMA-aligned", L.name, in_cs, in_coff, cip);
         return FVV_EINVAL;
     }
+    // circular padding: the layer reads a copy of its input window with a wrapped border
+    // of kCircPad pixels (TMA fills out-of-range coordinates with zeros only); the maps
+    // cover the padded image, the kernel shifts its A coordinates by the pad
+    int Hm = Hin, Wm = Win, ipad = 0;
+    if (h->o.pad_mode == FVV_PAD_CIRCULAR) {
+        const size_t need = (size_t)N * (Hin + 2 * kCircPad) * (Win + 2 * kCircPad) * cip * es;
+        if (need > h->cpad_bytes) {
+            set_error("layer %s: circular-pad buffer too small (%zu > %zu bytes)", L.name, need, h->cpad_bytes);
+            return FVV_ESHAPE;
+        }
+        FVV_TRY(launch_wrap_pad(in, N, count_word(h, li), Hin, Win, in_cs * es, in_coff * es, cip * es, kCircPad,
+                                h->cpad, st));
+        in = h->cpad; in_cs = cip; in_coff = 0;
+        Hm = Hin + 2 * kCircPad; Wm = Win + 2 * kCircPad; ipad = kCircPad;
+    }
     TcParams p{};
     p.mode = L.kind == K_CONVT ? (tc_all_phases(li) ? MODE_T3 : MODE_T) : (L.stride == 2 ? MODE_S2 : MODE_S1);
     p.n_img = N;
@@ -1678,6 +1692,7 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.err = h->d_err;
     p.stall_cycles = h->stall_now;
     p.n_dev = count_word(h, li);
+    p.ipad = ipad;
     if (epi) {
         p.epi = *epi;
         // the fused epilogues are written for the layers that use them
@@ -1696,9 +1711,9 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     int rc;
     if (p.mode == MODE_S2) {
         if (Hin % 2 || Win % 2) { g_encode_u8 = false; set_error("stride-2 layer %s needs even input size", L.name); return FVV_ESHAPE; }
-        cuuint64_t dims[5] = {(cuuint64_t)2 * in_cs, (cuuint64_t)Win / 2, 2, (cuuint64_t)Hin / 2, (cuuint64_t)N};
-        cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * e, (cuuint64_t)Win * in_cs * e,
-                                 (cuuint64_t)2 * Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
+        cuuint64_t dims[5] = {(cuuint64_t)2 * in_cs, (cuuint64_t)Wm / 2, 2, (cuuint64_t)Hm / 2, (cuuint64_t)N};
+        cuuint64_t strides[4] = {(cuuint64_t)2 * in_cs * e, (cuuint64_t)Wm * in_cs * e,
+                                 (cuuint64_t)2 * Wm * in_cs * e, (cuuint64_t)Hm * Wm * in_cs * e};
         if (s2h) { // 129 whole pixel pairs (2 x ck channels) of one input row
             cuuint32_t box[5] = {(cuuint32_t)(2 * ck), 129, 1, 1, 1};
             rc = encode(&ma, 5, (void *)in, dims, strides, box, 2 * ck * es);
@@ -1707,8 +1722,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             rc = encode(&ma, 5, (void *)in, dims, strides, box, ck * es);
         }
     } else {
-        cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Win, (cuuint64_t)Hin, (cuuint64_t)N};
-        cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Win * in_cs * e, (cuuint64_t)Hin * Win * in_cs * e};
+        cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Wm, (cuuint64_t)Hm, (cuuint64_t)N};
+        cuuint64_t strides[3] = {(cuuint64_t)in_cs * e, (cuuint64_t)Wm * in_cs * e, (cuuint64_t)Hm * Wm * in_cs * e};
         // halo boxes: MT rows x 130 pixels (folded column taps: 32 pixels, four per stage)
         cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)(kxf ? 32 : (halo ? tw_ + 2 : tw_)), (cuuint32_t)th_, 1};
         rc = encode(&ma, 4, (void *)in, dims, strides, box, ck * es);

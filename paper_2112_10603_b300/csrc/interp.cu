@@ -189,8 +189,9 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             T *tmp = src; src = dst; dst = tmp;
         }
         FVV_TRY(conv(h, base + 8, src, 256, 0, nv, hs / 4, ws / 4, ta, 128, 0, false, st));
-        if (b16 && s > 0) {
-            // Eq. 2 update fused into the last convT's epilogue
+        if (b16 && s > 0 && !circ) {
+            // Eq. 2 update fused into the last convT's epilogue (its x2 upsampling clamps at
+            // the border; circular mode runs the wrapping residual kernel instead)
             TcEpi e;
             e.mode = EPI_RESID;
             e.fm_prev = h->fm[s - 1];
@@ -316,6 +317,13 @@ static int create_impl(fvv_interp *h, const float *blob) {
     FVV_TRY(dalloc_t(h, &h->d_err, 64));
     FVV_TRY(dalloc_t(h, &h->d_outp, sizeof(float *)));
     FVV_TRY(dalloc_t(h, &h->d_cnt, 2 * sizeof(int)));
+    if (b16 && h->o.pad_mode == FVV_PAD_CIRCULAR) {
+        // wrapped-border copy of the largest conv input: a layer at 1/s of the padded grid
+        // reads at most 32 s^2 channels (VIB c0, c1, t1: 32 x P), with its 2-pixel border
+        // on each side: 32 (Hp + 4 s)(Wp + 4 s) elements, s <= 16
+        h->cpad_bytes = (size_t)(V > C ? V : C) * 32 * (Hp + 64) * (Wp + 64) * 2;
+        FVV_TRY(dalloc(h, &h->cpad, h->cpad_bytes));
+    }
     FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, 64));
     FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + (C + 1) * sizeof(float *) + 64));

@@ -103,6 +103,9 @@ struct fvv_interp {
     std::map<long long, Graph> graphs;
     int *d_cnt = nullptr;
     bool counts_live = false; // set while a bucket graph is captured
+    // circular mode on the tensor-core path: each conv's input window with a wrapped border
+    void *cpad = nullptr;
+    size_t cpad_bytes = 0;
     long long graph_captures = 0;
     cudaStream_t cap_stream = nullptr;
     // tile rectangle per layer: log2 of the tile width (-1: fewest-tiles default);
@@ -139,6 +142,9 @@ bool tc_kxf_layer(int layer);   // column taps folded into N (tiles of 120 pixel
 // transposed, all phases); their producers are the layer before (c0 .. t0) and write
 // E4M3 codes.
 inline bool fp8_layer(int li) { return li < kCtx && li % 10 >= 1; }
+// border (pixels) of the wrapped copies the tensor-core convs read in circular mode: even,
+// so that the stride-2 pixel-pair maps stay aligned to pairs
+constexpr int kCircPad = 2;
 // Device count word a conv layer's launch reads while a size-bucket graph is captured:
 // cameras for ContextNet's layers, views for every other layer; NULL otherwise.
 inline const int *count_word(const fvv_interp *h, int li) {

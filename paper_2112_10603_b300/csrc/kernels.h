@@ -46,5 +46,9 @@ int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, i
                     int h, int w, int circ, T *dst, int dst_cs, int off_l, int off_r, cudaStream_t st);
 int launch_output(const float *ib, const float *z, int z_cs, int nv, const int *nv_dev, int Hp, int Wp, int H, int W,
                   float *const *outp, cudaStream_t st);
+// Circular padding of a channel window (`bytes` per pixel from byte `coff_bytes` of pixels
+// `cs_bytes` apart) into a compact (H + 2 pad) x (W + 2 pad) image with wrapped borders.
+int launch_wrap_pad(const void *in, int N, const int *n_dev, int H, int W, int cs_bytes, int coff_bytes, int bytes,
+                    int pad, void *out, cudaStream_t st);
 
 } // namespace fvv

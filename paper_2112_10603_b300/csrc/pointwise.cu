@@ -318,6 +318,29 @@ __global__ void output_kernel(const float *ib, const float *z, int z_cs, int nv,
     }
 }
 
+// Circular padding for the tensor-core convolutions (whose TMA loads can only fill out-
+// of-range rows and columns with zeros): the channel window [coff, coff + chunks x 16 B)
+// of every pixel of n images, copied into an (H + 2 pad) x (W + 2 pad) image whose
+// border repeats the opposite edges (pixel (y, x) = input ((y - pad) mod H, (x - pad)
+// mod W)).  One thread per 16-byte chunk of the padded image.
+__global__ void wrap_pad_kernel(const uint8_t *__restrict__ in, int N, const int *n_dev, int H, int W, int cs_b,
+                                int coff_b, int chunks, int pad, uint8_t *__restrict__ out) {
+    N = dev_count(n_dev, N);
+    const int Hq = H + 2 * pad, Wq = W + 2 * pad;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * Hq * Wq * chunks) return;
+    const int j = (int)(idx % chunks);
+    long long r = idx / chunks;
+    const int x = (int)(r % Wq);
+    r /= Wq;
+    const int y = (int)(r % Hq), n = (int)(r / Hq);
+    int sy = (y - pad) % H, sx = (x - pad) % W;
+    sy += sy < 0 ? H : 0;
+    sx += sx < 0 ? W : 0;
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)n * H + sy) * W + sx) * cs_b + coff_b) + j);
+    reinterpret_cast<uint4 *>(out)[idx] = v;
+}
+
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 // 256-thread blocks over 32 x 8 pixel tiles (a warp = 32 pixels of one row)
 inline unsigned tile_blocks(int h, int w) { return (unsigned)(((w + 31) / 32) * ((h + 7) / 8)); }
@@ -376,6 +399,19 @@ int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, i
     long long n = (long long)h * w * (C / 8);
     ctx_warp_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(Fprev, fprev_cs, Fk, ctx, C, vt, nv, h, w, circ,
                                                            dst, dst_cs, off_l, off_r);
+    FVV_LAUNCH_CHECK();
+    return FVV_OK;
+}
+
+int launch_wrap_pad(const void *in, int N, const int *n_dev, int H, int W, int cs_bytes, int coff_bytes, int bytes,
+                    int pad, void *out, cudaStream_t st) {
+    if (cs_bytes % 16 || coff_bytes % 16 || bytes % 16 || ((uintptr_t)in % 16) || ((uintptr_t)out % 16)) {
+        set_error("circular pad: pixel stride, offset and width must be multiples of 16 bytes");
+        return FVV_EINVAL;
+    }
+    const long long n = (long long)N * (H + 2 * pad) * (W + 2 * pad) * (bytes / 16);
+    wrap_pad_kernel<<<blocks_for(n, 256), 256, 0, st>>>((const uint8_t *)in, N, n_dev, H, W, cs_bytes, coff_bytes,
+                                                        bytes / 16, pad, (uint8_t *)out);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }

@@ -119,3 +119,29 @@ def test_bf16_full_1080p_seven_views(torch_cuda):
     assert p >= PSNR_BF16, p
     alone = it.run(L, R, [ts[5]]).cpu().numpy()
     np.testing.assert_array_equal(alone[0], out[5])
+
+
+@pytest.mark.parametrize("H,W,shift", [(64, 96, (16, -48)), (32, 512, (-16, 272))])
+def test_bf16_circular_mode_and_shift_equivariance(H, W, shift):
+    """Circular padding on the tensor-core path: every conv reads a copy of its input
+    with a wrapped 2-pixel border (the TMA loads themselves can only zero-fill), the
+    Eq. 2 update runs in the wrapping residual kernel.  The BF16 forward is held to the
+    PSNR bar against the FP64 oracle in circular mode, and shifting both frames
+    cyclically by multiples of 16 pixels shifts the view bit for bit (every element's
+    arithmetic is the same wherever it lies).  32 x 512 puts the halo, folded-tap and
+    stride-2 pair-halo kernels on the wrapped inputs."""
+    import torch
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    left, right = pair(6, H, W, 6.0)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=1, pad_mode=fvv.FVV_PAD_CIRCULAR)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    a = it.run(L, R, [0.5]).cpu().numpy()[0]
+    fvv.fvv_interp_status(it.h)
+    ref, _ = oracle_view(6, H, W, 6.0, 0.5, circ=True)
+    assert psnr(a, ref) >= 45.0, psnr(a, ref)
+    Ls = torch.from_numpy(np.ascontiguousarray(np.roll(left, shift, (0, 1)))).cuda()
+    Rs = torch.from_numpy(np.ascontiguousarray(np.roll(right, shift, (0, 1)))).cuda()
+    b = it.run(Ls, Rs, [0.5]).cpu().numpy()[0]
+    np.testing.assert_array_equal(np.roll(a, shift, (0, 1)), b)
+    it.close()
