@@ -115,11 +115,15 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
     }
 }
 
-__device__ __forceinline__ void tile_coords(const TcParams &p, int n_img, int t, int &phase, int &n, int &y0,
-                                            int &x0) {
-    int per_phase = n_img * p.tiles_y * p.tiles_x;
-    phase = t / per_phase;
-    int r = t - phase * per_phase;
+// Tile t of a launch.  The 4 output phases of a per-phase transposed conv are the
+// innermost index: the four tiles of one pixel region run on neighbouring CTAs at the
+// same time and share its input in L2 (phase-major order streamed the whole input from
+// DRAM once per phase when it exceeds L2); with a grid that is a multiple of 4 every
+// persistent CTA also keeps one phase, i.e. one set of weight slices.
+__device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase, int &n, int &y0, int &x0) {
+    const int nph = p.mode == MODE_T ? 4 : 1;
+    phase = t % nph;
+    int r = t / nph;
     int tx = r % p.tiles_x;
     r /= p.tiles_x;
     int ty = r % p.tiles_y;
@@ -346,7 +350,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool stop = false;
             for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, n_img, t, ph, n, y0, x0);
+                tile_coords(p, t, ph, n, y0, x0);
                 for (int ky = 0; ky < 3; ++ky) {
                     if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
                     const uint32_t fs = ptx::smem_u32(&bars->full[s]);
@@ -390,7 +394,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool stop = false;
             for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, n_img, t, ph, n, y0, x0);
+                tile_coords(p, t, ph, n, y0, x0);
                 for (int ky = 0; ky < 3 && !stop; ++ky)
                     for (int c = 0; c < p.nck; ++c) {
                         if (!wait_bar(ptx::smem_u32(&bars->empty[s]), ph_bit ^ 1, abort, p.err, 1)) { stop = true; break; }
@@ -431,7 +435,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool stop = false;
             for (int t = blockIdx.x; t < num_tiles && !*abort && !stop; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, n_img, t, ph, n, y0, x0);
+                tile_coords(p, t, ph, n, y0, x0);
                 // boxes in K order (ky, channel block)
                 const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && !stop; ++grp) {
@@ -476,7 +480,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             long long issued = 0;
             for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
                 int ph, n, y0, x0;
-                tile_coords(p, n_img, t, ph, n, y0, x0);
+                tile_coords(p, t, ph, n, y0, x0);
                 for (int kb = 0; kb < kblocks; ++kb) {
                     if (!wait_bar(ptx::smem_u32(&bars->empty[stage]), phase_bit ^ 1, abort, p.err, 1)) break;
                     int tap = kb / p.nck, c0 = (kb - tap * p.nck) * CK;
@@ -747,7 +751,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
         for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
             int ph, n, y0, x0;
-            tile_coords(p, n_img, t, ph, n, y0, x0);
+            tile_coords(p, t, ph, n, y0, x0);
             int gy = y0 + dy, gx = x0 + dx;
             bool valid = gy < p.gh && gx < p.gw;
             uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (MT * BN);
