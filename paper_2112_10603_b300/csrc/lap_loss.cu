@@ -12,8 +12,9 @@
 // one-pixel halo need (edge-replicated) in shared memory, blurs them horizontally at
 // the even columns and vertically at the even rows, writes its G^(i+1) tile, and sums
 // |G^i - up(G^(i+1))| over its 2TY x 2TX pixels of level i (the halo supplies up()'s
-// neighbours).  Block sums go to a fixed slot; a last kernel adds them per view in a
-// fixed order (deterministic), adds ||G^5||_1 and weights the levels.
+// neighbours); the last level's kernel also sums |G^5| (= L^5) of its tiles.  Block sums
+// go to fixed slots; a last kernel adds them per view in a fixed order (deterministic)
+// and weights the levels.
 #include "common.h"
 
 namespace fvv {
@@ -24,6 +25,7 @@ constexpr int TY = 16, TX = 32;               // coarse tile of G^(i+1)
 constexpr int RY = 2 * TY + 7, RX = 2 * TX + 7; // staged rows / columns of G^i
 constexpr int GY = TY + 2, GX = TX + 2;        // G^(i+1) tile with its halo
 constexpr int kThreadsLap = 256;
+constexpr int kThreadsRed = 32 * 5; // final sums: one warp per level
 constexpr size_t kLapSmem = (size_t)(RY * RX * 3 + RY * GX * 3 + GY * GX * 3) * sizeof(float);
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
@@ -33,7 +35,7 @@ __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n
 template <bool FIRST>
 __global__ void __launch_bounds__(kThreadsLap)
 lap_level_kernel(const float *__restrict__ a, const float *__restrict__ b, int H, int W, float *__restrict__ g_next,
-                 int h, int w, int tiles_x, float *__restrict__ partial) {
+                 int h, int w, int tiles_x, float *__restrict__ partial, float *__restrict__ partial_next) {
     extern __shared__ float sm[];
     float *sD = sm;                      // RY x RX x 3: G^i around the tile, edge-replicated
     float *sT = sD + RY * RX * 3;        // RY x GX x 3: horizontal blur at even columns
@@ -78,6 +80,7 @@ lap_level_kernel(const float *__restrict__ a, const float *__restrict__ b, int H
     __syncthreads();
     // 3. vertical blur at the even rows -> G^(i+1) on the tile + halo; write the tile
     float *gn = g_next + (size_t)view * h * w * 3;
+    float acc_next = 0.f; // last level kernel: ||G^(i+1)||_1 of the tile (L^5 = G^5)
     for (int e = threadIdx.x; e < GY * GX; e += kThreadsLap) {
         const int i = e / GX, j = e - i * GX;
         const int cy = cy0 - 1 + i, cx = cx0 - 1 + j;
@@ -89,7 +92,10 @@ lap_level_kernel(const float *__restrict__ a, const float *__restrict__ b, int H
             const float g = k0 * t[ch] + k1 * t[GX * 3 + ch] + k2 * t[2 * GX * 3 + ch] + k1 * t[3 * GX * 3 + ch] +
                             k0 * t[4 * GX * 3 + ch];
             sG[e * 3 + ch] = g;
-            if (store) gn[((size_t)cy * w + cx) * 3 + ch] = g;
+            if (store) {
+                gn[((size_t)cy * w + cx) * 3 + ch] = g;
+                acc_next += fabsf(g);
+            }
         }
     }
     __syncthreads();
@@ -123,24 +129,34 @@ lap_level_kernel(const float *__restrict__ a, const float *__restrict__ b, int H
             if (x1 && y1) acc += fabsf(d[RX * 3 + 3 + ch] - oo);
         }
     }
-    // block sum (fixed order) -> partial[view][block]
+    // block sums (fixed order) -> partial[view][block] (and partial_next)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float wsum[kThreadsLap / 32];
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        acc_next += __shfl_xor_sync(0xffffffffu, acc_next, o);
+    }
+    __shared__ float wsum[2][kThreadsLap / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wsum[0][threadIdx.x >> 5] = acc;
+        wsum[1][threadIdx.x >> 5] = acc_next;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float s = 0.f;
+        float s = 0.f, s2 = 0.f;
 #pragma unroll
-        for (int i = 0; i < kThreadsLap / 32; ++i) s += wsum[i];
+        for (int i = 0; i < kThreadsLap / 32; ++i) {
+            s += wsum[0][i];
+            s2 += wsum[1][i];
+        }
         partial[(size_t)view * gridDim.x + blockIdx.x] = s;
+        if (partial_next) partial_next[(size_t)view * gridDim.x + blockIdx.x] = s2;
     }
 }
 
 struct LapPlan {
     int h[kLevels], w[kLevels];     // size of level i (0-based: G^1 .. G^5)
     int blocks[kLevels - 1];        // blocks per view of the level kernels
-    size_t g_off[kLevels], p_off[kLevels - 1], bytes;
+    size_t g_off[kLevels], p_off[kLevels], bytes; // p_off[4]: ||G^5||_1 per block of the last level kernel
 };
 
 __host__ LapPlan lap_plan(int n, int H, int W) {
@@ -158,44 +174,38 @@ __host__ LapPlan lap_plan(int n, int H, int W) {
         P.p_off[i] = off;
         off += al((size_t)n * P.blocks[i] * sizeof(float));
     }
+    P.p_off[kLevels - 1] = off;
+    off += al((size_t)n * P.blocks[kLevels - 2] * sizeof(float));
     P.bytes = off;
     return P;
 }
 
 struct LapSums {
-    const float *part[kLevels - 1];
-    int blocks[kLevels - 1];
-    const float *g5;
-    int n5; // elements of G^5 per view
+    const float *part[kLevels]; // block sums of L^1 .. L^4, and of |G^5| (= L^5)
+    int blocks[kLevels];
 };
 
-// One block per view: the level sums in a fixed order (double), ||G^5||_1, the loss.
-__global__ void lap_reduce_kernel(const LapSums s, float *loss, float *norms) {
-    __shared__ double red[kThreadsLap];
-    const int view = blockIdx.x;
-    double tot = 0.0;
-    for (int lv = 0; lv < kLevels; ++lv) {
-        double acc = 0.0;
-        if (lv < kLevels - 1) {
-            const float *p = s.part[lv] + (size_t)view * s.blocks[lv];
-            for (int i = threadIdx.x; i < s.blocks[lv]; i += kThreadsLap) acc += p[i];
-        } else {
-            const float *g = s.g5 + (size_t)view * s.n5;
-            for (int i = threadIdx.x; i < s.n5; i += kThreadsLap) acc += fabsf(g[i]);
-        }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int o = kThreadsLap / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            if (norms) norms[(size_t)view * kLevels + lv] = (float)red[0];
-            tot += ldexp(red[0], lv); // weight 2^(i-1), i counted from 1
-        }
-        __syncthreads();
+// One block per view, one warp per level: the level's block sums in a fixed order
+// (double: lane-strided, then a fixed shuffle tree), then the weighted loss.
+__global__ void __launch_bounds__(kThreadsRed) lap_reduce_kernel(const LapSums s, float *loss, float *norms) {
+    __shared__ double lvl[kLevels];
+    const int view = blockIdx.x, lv = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    const float *p = s.part[lv] + (size_t)view * s.blocks[lv];
+    for (int i = lane; i < s.blocks[lv]; i += 32) acc += p[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        lvl[lv] = acc;
+        if (norms) norms[(size_t)view * kLevels + lv] = (float)acc;
     }
-    if (threadIdx.x == 0 && loss) loss[view] = (float)tot;
+    __syncthreads();
+    if (threadIdx.x == 0 && loss) {
+        double tot = 0.0;
+#pragma unroll
+        for (int i = 0; i < kLevels; ++i) tot += ldexp(lvl[i], i); // weight 2^(i-1), i counted from 1
+        loss[view] = (float)tot;
+    }
 }
 
 } // namespace
@@ -241,19 +251,22 @@ extern "C" int fvv_lap_loss(const float *pred, const float *gt, int n, int H, in
         float *part = (float *)(ws + P.p_off[lv]);
         const int tiles_x = ceil_div(P.w[lv + 1], TX);
         dim3 grid(P.blocks[lv], n);
+        // the last level kernel also sums |G^5| (= L^5) of its tiles
+        float *part_next = lv == kLevels - 2 ? (float *)(ws + P.p_off[kLevels - 1]) : nullptr;
         if (lv == 0)
             lap_level_kernel<true><<<grid, kThreadsLap, kLapSmem, st>>>(src, gt, P.h[lv], P.w[lv], dst, P.h[lv + 1],
-                                                                        P.w[lv + 1], tiles_x, part);
+                                                                        P.w[lv + 1], tiles_x, part, part_next);
         else
             lap_level_kernel<false><<<grid, kThreadsLap, kLapSmem, st>>>(src, nullptr, P.h[lv], P.w[lv], dst,
-                                                                         P.h[lv + 1], P.w[lv + 1], tiles_x, part);
+                                                                         P.h[lv + 1], P.w[lv + 1], tiles_x, part,
+                                                                         part_next);
         FVV_CHECK_CUDA(cudaGetLastError());
         sums.part[lv] = part;
         sums.blocks[lv] = P.blocks[lv];
     }
-    sums.g5 = (const float *)(ws + P.g_off[kLevels - 1]);
-    sums.n5 = P.h[kLevels - 1] * P.w[kLevels - 1] * 3;
-    lap_reduce_kernel<<<n, kThreadsLap, 0, st>>>(sums, loss, level_norms);
+    sums.part[kLevels - 1] = (const float *)(ws + P.p_off[kLevels - 1]);
+    sums.blocks[kLevels - 1] = P.blocks[kLevels - 2];
+    lap_reduce_kernel<<<n, kThreadsRed, 0, st>>>(sums, loss, level_norms);
     FVV_CHECK_CUDA(cudaGetLastError());
     return FVV_OK;
 }
