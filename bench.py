@@ -796,7 +796,7 @@ def conv_roofline(precision, lms, lfl, lln, ms_prof, pk, pk_kind, views, fp8_pea
     vib2m = [names.index(f"vib2.m{k}") for k in range(6)]
     m_ms, m_fl, m_n = float(lms[vib2m].sum()), float(lfl[vib2m].sum()), int(lln[vib2m].sum())
     if precision == "fp32":
-        roof = {"bound": "alu", "kernel": "conv_simt_kernel (FP32 FFMA implicit GEMM), all layers",
+        roof = {"bound": "alu", "kernel": "conv_simt_vec_kernel / conv_simt_kernel (FP32 FFMA implicit GEMM), all layers",
                 "achieved": conv_fl / (conv_ms / 1e3) / 1e12, "peak": FP32_FFMA_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz", "traffic": None}
     elif precision == "fp8":
