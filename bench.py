@@ -192,14 +192,15 @@ def rig_measure(precision, warmup, steps, rank=0):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     ev = []
-    for i, (offs, ts) in enumerate(instants):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        it.run_batch(cams, pairs, offs, ts, out=out)
-        b.record(stream)
-        if i >= warmup:
-            ev.append((a, b, int(offs[-1])))
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i, (offs, ts) in enumerate(instants):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            it.run_batch(cams, pairs, offs, ts, out=out)
+            b.record(stream)
+            if i >= warmup:
+                ev.append((a, b, int(offs[-1])))
+        torch.cuda.synchronize()
     ms = np.array([a.elapsed_time(b) for a, b, _ in ev])
     views = int(sum(v for _, _, v in ev))
     line = {"metric": METRIC + " (rig instant, batched)", "value": views / (ms.sum() / 1e3), "unit": "views/s",
@@ -211,6 +212,7 @@ def rig_measure(precision, warmup, steps, rank=0):
             "ms_per_instant": {"mean": float(ms.mean()), "p50": float(np.percentile(ms, 50)),
                                "p99": float(np.percentile(ms, 99)), "max": float(ms.max())},
             "views_per_instant_mean": views / len(ev), "gpu_launches_per_instant": it.last_launches,
+            "clocks": clk.summary(),
             "graph_captures": it.graph_captures, "distinct_view_counts": len({int(o[-1]) for o, _ in instants})}
     it.close()
     del out, cams
