@@ -33,6 +33,7 @@
 #include "interp.h"
 #include "sampling.h"
 #include "tc_ptx.h"
+#include "tc_wait.h"
 
 namespace fvv {
 
@@ -43,8 +44,6 @@ namespace {
 // columns; each phase's weights are zero on the 5 taps it does not use).
 enum { MODE_S1 = 0, MODE_S2 = 1, MODE_T = 2, MODE_T3 = 3 };
 constexpr int kThreads = 192;
-constexpr long long kWaitCycles = 4000000000ll; // ~2 s: far beyond any legitimate wait
-constexpr uint32_t kSleepNs = 20000;             // suspend-time hint of a waiting thread
 
 struct TcParams {
     int mode;
@@ -98,23 +97,6 @@ struct __align__(8) Bars {
     int abort;
 };
 
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort, int *err, int code,
-                                         long long limit = kWaitCycles) {
-    long long t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (ptx::mbar_try_wait_hint(bar, parity, kSleepNs)) return true;
-        if ((it & 255) == 255) {
-            if (*abort) return false;
-            long long now = clock64();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > limit) {
-                *abort = 1;
-                atomicExch(err, code);
-                return false;
-            }
-        }
-    }
-}
 
 // Tile t of a launch.  The 4 output phases of a per-phase transposed conv are the
 // innermost index: the four tiles of one pixel region run on neighbouring CTAs at the

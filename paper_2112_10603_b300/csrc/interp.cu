@@ -145,6 +145,30 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
     return launch_conv_simt(a, false, is_bf16(h) && !out_f32, st);
 }
 
+// The VIB1 / VIB2 input conv with the stage input computed in its loader: tensor-core
+// handles, unless a tile width is forced for the layer (the autotuner's candidates and the
+// tile cache then run the stage-input kernel and the conv apart).
+static bool stage_fused(const fvv_interp *h, int li) {
+    return is_bf16(h) && stage_conv_layer(h, li) && h->tile_force < 0 && h->tile_tw[li] < 0;
+}
+
+// The fused stage input + c0 launch, bracketed by events (as layer c0) while profiling.
+static int stage_conv(fvv_interp *h, int li, const float4 *imgs, const float *fm_prev, const ViewTab &vt, int nv,
+                      int hs, int ws, int circ, void *out, cudaStream_t st) {
+    if (!h->profiling) return tc_stage_conv(h, li, imgs, fm_prev, vt, nv, hs, ws, circ, out, 128, st);
+    const LayerDef &L = kLayers[li];
+    fvv_interp::ProfRec r;
+    r.layer = li;
+    r.flops = 2.0 * nv * (hs / 2) * (ws / 2) * L.co * 9.0 * L.ci;
+    r.a = pool_event(h);
+    r.b = pool_event(h);
+    FVV_CHECK_CUDA(cudaEventRecord(r.a, st));
+    int rc = tc_stage_conv(h, li, imgs, fm_prev, vt, nv, hs, ws, circ, out, 128, st);
+    FVV_CHECK_CUDA(cudaEventRecord(r.b, st));
+    h->prof.push_back(r);
+    return rc;
+}
+
 template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cudaStream_t st) {
     const int Hp = h->Hp, Wp = h->Wp, circ = h->o.pad_mode == FVV_PAD_CIRCULAR;
     const bool b16 = is_bf16(h);
@@ -178,10 +202,15 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
         int cx = s == 0 ? cx0 : cx1;
         // VIB0's input has its own buffer: each layout keeps its zero padding channels
         T *x = s == 0 ? (T *)h->xb0 : xb;
-        if (s == 0) FVV_TRY(launch_vib0_input<T>(h->img2, vt, nv, hs, ws, x, cx, st));
-        else FVV_TRY(launch_stage_input<T>(s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, x, cx, st));
         int base = s * 10;
-        FVV_TRY(conv(h, base + 0, x, cx, 0, nv, hs, ws, ta, 128, 0, false, st));
+        if (s > 0 && stage_fused(h, base)) {
+            // a3 inside c0's loader: the stage input is never stored
+            FVV_TRY(stage_conv(h, base, s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, ta, st));
+        } else {
+            if (s == 0) FVV_TRY(launch_vib0_input<T>(h->img2, vt, nv, hs, ws, x, cx, st));
+            else FVV_TRY(launch_stage_input<T>(s == 1 ? h->img1 : h->img0, h->fm[s - 1], vt, nv, hs, ws, circ, x, cx, st));
+            FVV_TRY(conv(h, base + 0, x, cx, 0, nv, hs, ws, ta, 128, 0, false, st));
+        }
         FVV_TRY(conv(h, base + 1, ta, 128, 0, nv, hs / 2, ws / 2, ma, 256, 0, false, st));
         T *src = ma, *dst = mb;
         for (int k = 0; k < 6; ++k) {
@@ -899,6 +928,10 @@ int fvv_interp_autotune(fvv_interp *h, int n_views, const char *cache_path) {
     h->tile_force = -1;
     fvv_interp_profile(h, was_profiling ? 1 : 0);
     if (rc != FVV_OK) return rc;
+    // the stage-input convs keep the fused kernel: their default timing includes the stage
+    // input, the candidates' does not, so the two are not comparable
+    for (int i = 0; i < kNumLayers; ++i)
+        if (stage_conv_layer(h, i)) pick[i] = -1;
     for (int i = 0; i < kNumLayers; ++i) h->tile_tw[i] = (signed char)pick[i];
     if (cache_path) {
         std::string obj = "{";

@@ -135,6 +135,12 @@ int dalloc(fvv_interp *h, void **p, size_t bytes);
 int tc_prepare(fvv_interp *h, const float *blob);
 int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, int N, int Hin, int Win,
             void *out, int out_cs, int out_coff, bool out_f32, cudaStream_t st, const TcEpi *epi = nullptr);
+// VIBlock s > 0: the stage input (x2 upsampled F, M of the previous stage, both frames
+// warped, the frames, t) computed by the loader of the block's first conv (c0) itself;
+// out: the c0 output (bf16, or E4M3 for an FP8 consumer), out_cs = 128
+bool stage_conv_layer(const fvv_interp *h, int layer);
+int tc_stage_conv(fvv_interp *h, int layer, const float4 *imgs, const float *fm_prev, const ViewTab &vt, int nv,
+                  int hs, int ws, int circ, void *out, int out_cs, cudaStream_t st);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
 bool tc_kxf_layer(int layer);   // column taps folded into N (tiles of 120 pixels)
 // FP8 layers: every VIBlock conv with 128 or 256 input channels -- c1 (128 -> 256,

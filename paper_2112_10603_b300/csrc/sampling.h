@@ -58,6 +58,18 @@ __device__ __forceinline__ float bilerp(const T *img, int cs, int c, const Taps 
     return (1.f - t.ly) * ((1.f - t.lx) * a + t.lx * b) + t.ly * ((1.f - t.lx) * d + t.lx * e);
 }
 
+// Frame pyramid levels hold one float4 (R, G, B, 0) per pixel: one 16-byte load per
+// bilinear tap.  Same arithmetic, channel by channel, as bilerp().
+__device__ __forceinline__ float3 bilerp_rgb(const float4 *img, const Taps &t) {
+    float4 a = __ldg(img + t.o00), b = __ldg(img + t.o01), d = __ldg(img + t.o10), e = __ldg(img + t.o11);
+    const float wx0 = 1.f - t.lx, wy0 = 1.f - t.ly;
+    float3 r;
+    r.x = wy0 * (wx0 * a.x + t.lx * b.x) + t.ly * (wx0 * d.x + t.lx * e.x);
+    r.y = wy0 * (wx0 * a.y + t.lx * b.y) + t.ly * (wx0 * d.y + t.lx * e.y);
+    r.z = wy0 * (wx0 * a.z + t.lx * b.z) + t.ly * (wx0 * d.z + t.lx * e.z);
+    return r;
+}
+
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 
 } // namespace fvv
