@@ -126,9 +126,9 @@ __device__ __forceinline__ bool tile_pixel(int h, int w, int &X, int &Y) {
 // at the stage grid h x w, from the previous stage's flow/mask FMp (h/2 x w/2 x 5).
 // One thread per pixel walks the views: views of one camera pair gather the same
 // image neighbourhoods, which then come from L1/L2 instead of DRAM once per view.
-template <typename T>
+template <typename T, bool CIRC>
 __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const ViewTab vt, int nv,
-                                   int h, int w, int circ, T *x, int cs) {
+                                   int h, int w, T *x, int cs) {
     nv = dev_count(vt.n, nv);
     const long long P = (long long)h * w;
     int X, Y;
@@ -137,7 +137,7 @@ __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const V
     for (int v = 0; v < nv; ++v) {
     const long long idx = v * P + p;
     const float *fm = FMp + (size_t)v * (P / 4) * 5;
-    Taps u = up_taps(X, Y, h / 2, w / 2, circ);
+    Taps u = up_taps_t<CIRC>(X, Y, h / 2, w / 2);
     float up[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) up[c] = bilerp(fm, 5, c, u);
@@ -145,8 +145,8 @@ __global__ void stage_input_kernel(const float4 *imgs, const float *FMp, const V
     for (int c = 0; c < 4; ++c) up[c] *= 2.f;
     const float4 *L = imgs + (size_t)vt.cam_l[v] * P;
     const float4 *R = imgs + (size_t)vt.cam_r[v] * P;
-    Taps tl = warp_taps(X, Y, up[0], up[1], h, w, circ);
-    Taps tr = warp_taps(X, Y, up[2], up[3], h, w, circ);
+    Taps tl = warp_taps_t<CIRC>(X, Y, up[0], up[1], h, w);
+    Taps tr = warp_taps_t<CIRC>(X, Y, up[2], up[3], h, w);
     const float4 lc = __ldg(L + p), rc = __ldg(R + p);
     const float3 wl = bilerp_rgb(L, tl), wr = bilerp_rgb(R, tr);
     float vals[18] = {lc.x, lc.y, lc.z, rc.x, rc.y, rc.z, wl.x, wl.y, wl.z, wr.x, wr.y, wr.z};
@@ -177,9 +177,9 @@ __global__ void residual_kernel(const float *FMp, float *res, int nv, const int 
 // a5 (Eq. 1): I_l->m, I_r->m by the final flows, M = sigmoid(logit), blend.
 // Writes the refinement input [I_l->m, I_r->m] (zero-padded to cs) and I_blend.
 // One thread per pixel walks the views (image taps shared across views stay in cache).
-template <typename T>
+template <typename T, bool CIRC>
 __global__ void final_blend_kernel(const float4 *__restrict__ img0, const float *__restrict__ FM, const ViewTab vt,
-                                   int nv, int h, int w, int circ, T *__restrict__ u0, int cs, float *__restrict__ ib) {
+                                   int nv, int h, int w, T *__restrict__ u0, int cs, float *__restrict__ ib) {
     nv = dev_count(vt.n, nv);
     const long long P = (long long)h * w;
     int X, Y;
@@ -192,8 +192,8 @@ __global__ void final_blend_kernel(const float4 *__restrict__ img0, const float 
     const float *f = FM + (size_t)idx * 5;
     const float4 *L = img0 + (size_t)vt.cam_l[v] * P;
     const float4 *R = img0 + (size_t)vt.cam_r[v] * P;
-    Taps tl = warp_taps(X, Y, f[0], f[1], h, w, circ);
-    Taps tr = warp_taps(X, Y, f[2], f[3], h, w, circ);
+    Taps tl = warp_taps_t<CIRC>(X, Y, f[0], f[1], h, w);
+    Taps tr = warp_taps_t<CIRC>(X, Y, f[2], f[3], h, w);
     float M = sigmoidf_(f[4]);
     const float3 a = bilerp_rgb(L, tl), b = bilerp_rgb(R, tr);
     float vals[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
@@ -247,27 +247,29 @@ __device__ __forceinline__ void store8(bf16 *d, const float (&v)[8]) {
 // by F_k[0:2] / F_k[2:4] into channel slots of the U-Net level tensor.
 // One thread per (pixel, group of 8 channels) walks the views (the context features
 // of a camera are gathered by every view that uses it).
-template <typename T>
-__global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C,
-                                const ViewTab vt, int nv, int h, int w, int circ,
+// (glog = log2(C / 8): groups of 8 channels per pixel; every index fits in 32 bits)
+template <typename T, bool CIRC>
+__global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, int glog,
+                                const ViewTab vt, int nv, int h, int w,
                                 T *dst, int dst_cs, int off_l, int off_r) {
     nv = dev_count(vt.n, nv);
-    const int groups = C / 8;
-    const long long P = (long long)h * w;
-    const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= P * groups) return;
-    const int g = (int)(gi % groups);
-    const int p = (int)(gi / groups);
+    const int P = h * w;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= (P << glog)) return;
+    const int g = gi & ((1 << glog) - 1);
+    const int p = gi >> glog;
     const int X = p % w, Y = p / w;
+    const int W2 = 2 * w;
+    // the 2 x 2 block of the finer flow level under this pixel
+    const int i00 = (2 * Y * W2 + 2 * X) * fprev_cs, i01 = i00 + fprev_cs, i10 = i00 + W2 * fprev_cs,
+              i11 = i10 + fprev_cs;
     for (int v = 0; v < nv; ++v) {
-    const long long vp = v * P + p;
+    const size_t vp = (size_t)v * P + p;
     const float *fp = Fprev + (size_t)v * (P * 4) * fprev_cs;
-    int W2 = 2 * w;
     float F[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        float s = fp[((size_t)(2 * Y) * W2 + 2 * X) * fprev_cs + c] + fp[((size_t)(2 * Y) * W2 + 2 * X + 1) * fprev_cs + c] +
-                  fp[((size_t)(2 * Y + 1) * W2 + 2 * X) * fprev_cs + c] + fp[((size_t)(2 * Y + 1) * W2 + 2 * X + 1) * fprev_cs + c];
+        float s = fp[i00 + c] + fp[i01 + c] + fp[i10 + c] + fp[i11 + c];
         F[c] = s * 0.25f * 0.5f;
     }
     if (g == 0) {
@@ -276,8 +278,8 @@ __global__ void ctx_warp_kernel(const float *Fprev, int fprev_cs, float *Fk, con
     }
     const T *cl = ctx + (size_t)vt.cam_l[v] * P * C;
     const T *cr = ctx + (size_t)vt.cam_r[v] * P * C;
-    Taps tl = warp_taps(X, Y, F[0], F[1], h, w, circ);
-    Taps tr = warp_taps(X, Y, F[2], F[3], h, w, circ);
+    Taps tl = warp_taps_t<CIRC>(X, Y, F[0], F[1], h, w);
+    Taps tr = warp_taps_t<CIRC>(X, Y, F[2], F[3], h, w);
     T *d = dst + (size_t)vp * dst_cs;
     float o[8];
     bilerp8(cl, C, g * 8, tl, o);
@@ -360,7 +362,8 @@ int launch_vib0_input(const float4 *img2, const ViewTab &vt, int nv, int h, int 
 template <typename T>
 int launch_stage_input(const float4 *imgs, const float *FMp, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *x, int cs, cudaStream_t st) {
-    stage_input_kernel<T><<<tile_blocks(h, w), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, circ, x, cs);
+    if (circ) stage_input_kernel<T, true><<<tile_blocks(h, w), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, x, cs);
+    else stage_input_kernel<T, false><<<tile_blocks(h, w), 256, 0, st>>>(imgs, FMp, vt, nv, h, w, x, cs);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
@@ -376,7 +379,8 @@ int launch_residual(const float *FMp, float *res, int nv, const int *nv_dev, int
 template <typename T>
 int launch_final_blend(const float4 *img0, const float *FM, const ViewTab &vt, int nv, int h, int w,
                        int circ, T *u0, int cs, float *ib, cudaStream_t st) {
-    final_blend_kernel<T><<<tile_blocks(h, w), 256, 0, st>>>(img0, FM, vt, nv, h, w, circ, u0, cs, ib);
+    if (circ) final_blend_kernel<T, true><<<tile_blocks(h, w), 256, 0, st>>>(img0, FM, vt, nv, h, w, u0, cs, ib);
+    else final_blend_kernel<T, false><<<tile_blocks(h, w), 256, 0, st>>>(img0, FM, vt, nv, h, w, u0, cs, ib);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }
@@ -385,8 +389,18 @@ template <typename T>
 int launch_ctx_warp(const float *Fprev, int fprev_cs, float *Fk, const T *ctx, int C, const ViewTab &vt,
                     int nv, int h, int w, int circ, T *dst, int dst_cs, int off_l, int off_r, cudaStream_t st) {
     long long n = (long long)h * w * (C / 8);
-    ctx_warp_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(Fprev, fprev_cs, Fk, ctx, C, vt, nv, h, w, circ,
-                                                           dst, dst_cs, off_l, off_r);
+    int glog = 0;
+    while ((8 << glog) < C) ++glog;
+    if ((8 << glog) != C || 4ll * h * w * fprev_cs >= (1ll << 31) || n >= (1ll << 31)) {
+        set_error("context warp: C must be 8 x a power of two, the level below 2^31 elements");
+        return FVV_ESHAPE;
+    }
+    if (circ)
+        ctx_warp_kernel<T, true><<<blocks_for(n, 256), 256, 0, st>>>(Fprev, fprev_cs, Fk, ctx, C, glog, vt, nv, h, w,
+                                                                     dst, dst_cs, off_l, off_r);
+    else
+        ctx_warp_kernel<T, false><<<blocks_for(n, 256), 256, 0, st>>>(Fprev, fprev_cs, Fk, ctx, C, glog, vt, nv, h, w,
+                                                                      dst, dst_cs, off_l, off_r);
     FVV_LAUNCH_CHECK();
     return FVV_OK;
 }

@@ -51,6 +51,36 @@ __device__ __forceinline__ Taps up_taps(int X, int Y, int h, int w, int circ) {
     return t;
 }
 
+// The same taps with the padding mode fixed at compile time (no per-index branch).
+template <bool CIRC> __device__ __forceinline__ int fix_index_t(int i, int n) {
+    if (CIRC) { i %= n; return i < 0 ? i + n : i; }
+    return min(max(i, 0), n - 1);
+}
+template <bool CIRC> __device__ __forceinline__ Taps warp_taps_t(int x, int y, float fx, float fy, int H, int W) {
+    const float lim = CIRC ? 16777216.f : (float)(max(H, W) + 4);
+    fx = fminf(fmaxf(fx, -lim), lim);
+    fy = fminf(fmaxf(fy, -lim), lim);
+    const float flx = floorf(fx), fly = floorf(fy);
+    Taps t;
+    t.lx = fx - flx;
+    t.ly = fy - fly;
+    const int x0 = x + (int)flx, y0 = y + (int)fly;
+    const int xa = fix_index_t<CIRC>(x0, W), xb = fix_index_t<CIRC>(x0 + 1, W);
+    const int ya = fix_index_t<CIRC>(y0, H), yb = fix_index_t<CIRC>(y0 + 1, H);
+    t.o00 = ya * W + xa; t.o01 = ya * W + xb; t.o10 = yb * W + xa; t.o11 = yb * W + xb;
+    return t;
+}
+template <bool CIRC> __device__ __forceinline__ Taps up_taps_t(int X, int Y, int h, int w) {
+    Taps t;
+    const int x0 = (X >> 1) - ((X & 1) ? 0 : 1), y0 = (Y >> 1) - ((Y & 1) ? 0 : 1);
+    t.lx = (X & 1) ? 0.25f : 0.75f;
+    t.ly = (Y & 1) ? 0.25f : 0.75f;
+    const int xa = fix_index_t<CIRC>(x0, w), xb = fix_index_t<CIRC>(x0 + 1, w);
+    const int ya = fix_index_t<CIRC>(y0, h), yb = fix_index_t<CIRC>(y0 + 1, h);
+    t.o00 = ya * w + xa; t.o01 = ya * w + xb; t.o10 = yb * w + xa; t.o11 = yb * w + xb;
+    return t;
+}
+
 template <typename T>
 __device__ __forceinline__ float bilerp(const T *img, int cs, int c, const Taps &t) {
     float a = to_f(img[(size_t)t.o00 * cs + c]), b = to_f(img[(size_t)t.o01 * cs + c]);

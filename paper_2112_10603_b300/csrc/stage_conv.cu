@@ -89,37 +89,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return u;
 }
 
-// Index helpers of the sampling conventions (the shared ones in sampling.h), with the
-// padding mode fixed at compile time; the same taps and weights, so the same values.
-template <bool CIRC> __device__ __forceinline__ int fixi(int i, int n) {
-    if (CIRC) { i %= n; return i < 0 ? i + n : i; }
-    return min(max(i, 0), n - 1);
-}
-template <bool CIRC> __device__ __forceinline__ Taps warp_taps_c(int x, int y, float fx, float fy, int H, int W) {
-    const float lim = CIRC ? 16777216.f : (float)(max(H, W) + 4);
-    fx = fminf(fmaxf(fx, -lim), lim);
-    fy = fminf(fmaxf(fy, -lim), lim);
-    const float flx = floorf(fx), fly = floorf(fy);
-    Taps t;
-    t.lx = fx - flx;
-    t.ly = fy - fly;
-    const int x0 = x + (int)flx, y0 = y + (int)fly;
-    const int xa = fixi<CIRC>(x0, W), xb = fixi<CIRC>(x0 + 1, W);
-    const int ya = fixi<CIRC>(y0, H), yb = fixi<CIRC>(y0 + 1, H);
-    t.o00 = ya * W + xa; t.o01 = ya * W + xb; t.o10 = yb * W + xa; t.o11 = yb * W + xb;
-    return t;
-}
-template <bool CIRC> __device__ __forceinline__ Taps up_taps_c(int X, int Y, int h, int w) {
-    Taps t;
-    const int x0 = (X >> 1) - ((X & 1) ? 0 : 1), y0 = (Y >> 1) - ((Y & 1) ? 0 : 1);
-    t.lx = (X & 1) ? 0.25f : 0.75f;
-    t.ly = (Y & 1) ? 0.25f : 0.75f;
-    const int xa = fixi<CIRC>(x0, w), xb = fixi<CIRC>(x0 + 1, w);
-    const int ya = fixi<CIRC>(y0, h), yb = fixi<CIRC>(y0 + 1, h);
-    t.o00 = ya * w + xa; t.o01 = ya * w + xb; t.o10 = yb * w + xa; t.o11 = yb * w + xb;
-    return t;
-}
-
 // The 18 stage-input channels of pixel (X, Y[r]) of view v, for NR rows at once (their
 // gathers in flight together), as three 16-byte chunks of bf16 each (channels 0-7, 8-15,
 // 16-23; 18-23 are zero): the standalone stage-input kernel's arithmetic.  The
@@ -136,7 +105,7 @@ __device__ __forceinline__ void stage_pixels(const ScParams &p, int v, int X, co
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         // x2 upsampling of the previous stage's F, M: the four taps' 5 channels each
-        const Taps u = up_taps_c<CIRC>(X, Y[r], h / 2, w / 2);
+        const Taps u = up_taps_t<CIRC>(X, Y[r], h / 2, w / 2);
         const float *a = fm + u.o00 * 5, *b = fm + u.o01 * 5, *d = fm + u.o10 * 5, *e = fm + u.o11 * 5;
 #pragma unroll
         for (int k = 0; k < 5; ++k)
@@ -148,8 +117,8 @@ __device__ __forceinline__ void stage_pixels(const ScParams &p, int v, int X, co
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int pix = Y[r] * w + X;
-        const Taps tl = warp_taps_c<CIRC>(X, Y[r], up[r][0], up[r][1], h, w);
-        const Taps tr = warp_taps_c<CIRC>(X, Y[r], up[r][2], up[r][3], h, w);
+        const Taps tl = warp_taps_t<CIRC>(X, Y[r], up[r][0], up[r][1], h, w);
+        const Taps tr = warp_taps_t<CIRC>(X, Y[r], up[r][2], up[r][3], h, w);
         const float4 lc = __ldg(L + pix), rc = __ldg(R + pix);
         const float3 wl = bilerp_rgb(L, tl), wr = bilerp_rgb(R, tr);
         c[r][0] = make_uint4(pack_bf16x2(lc.x, lc.y), pack_bf16x2(lc.z, rc.x), pack_bf16x2(rc.y, rc.z),
@@ -431,14 +400,14 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
                 // padding) computed from clamped coordinates, or wrapped (circular)
                 const int X0 = 2 * x0 - 2 + i;
                 const bool xin = CIRC || (X0 >= 0 && X0 < p.w);
-                const int X = fixi<CIRC>(X0, p.w);
+                const int X = fix_index_t<CIRC>(X0, p.w);
                 int Y[2];
                 bool yin[2];
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int Y0 = 2 * y + (nr == 3 ? j : j + 1) - 1;
                     yin[j] = CIRC || (Y0 >= 0 && Y0 < p.h);
-                    Y[j] = fixi<CIRC>(Y0, p.h);
+                    Y[j] = fix_index_t<CIRC>(Y0, p.h);
                 }
                 uint4 cv[2][3];
                 stage_pixels<CIRC, 2>(p, n, X, Y, cv);
@@ -446,7 +415,7 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
                 put(rg[1].slot, cv[1], xin && yin[1]);
                 if (nr == 3) {
                     const int Y0 = 2 * y + 1;
-                    const int Y1[1] = {fixi<CIRC>(Y0, p.h)};
+                    const int Y1[1] = {fix_index_t<CIRC>(Y0, p.h)};
                     uint4 c1[1][3];
                     stage_pixels<CIRC, 1>(p, n, X, Y1, c1);
                     put(rg[2].slot, c1[0], xin && (CIRC || Y0 < p.h));
