@@ -45,11 +45,33 @@ namespace {
 enum { MODE_S1 = 0, MODE_S2 = 1, MODE_T = 2, MODE_T3 = 3 };
 constexpr int kThreads = 192;
 
+// Unsigned division by a divisor fixed at launch, as a multiply-high and shifts
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994,
+// the round-up method for N = 32): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n); exact for
+// every 32-bit n.
+struct FastDiv {
+    uint32_t d = 1, m = 1, s1 = 0, s2 = 0;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div) {
+        uint32_t l = 0;
+        while ((1ull << l) < div) ++l;
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+        s1 = l < 1 ? l : 1;
+        s2 = l > 1 ? l - 1 : 0;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        const uint32_t t = __umulhi(m, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+};
+
 struct TcParams {
     int mode;
     int n_img, gh, gw;      // GEMM grid (conv: output size; convT: input size)
     int th_log, tw_log;     // tile = (1 << th_log) x (1 << tw_log) = 128 pixels
     int tiles_y, tiles_x, num_tiles;
+    FastDiv fdx, fdy;       // division by tiles_x, tiles_y
     int nck;                // channel blocks per tap
     int taps;               // 9 (conv, MODE_T3) or 4 (convT phase)
     int in_cs, in_coff;     // input pixel stride / channel offset (elements)
@@ -104,13 +126,12 @@ struct __align__(8) Bars {
 // DRAM once per phase when it exceeds L2); with a grid that is a multiple of 4 every
 // persistent CTA also keeps one phase, i.e. one set of weight slices.
 __device__ __forceinline__ void tile_coords(const TcParams &p, int t, int &phase, int &n, int &y0, int &x0) {
-    const int nph = p.mode == MODE_T ? 4 : 1;
-    phase = t % nph;
-    int r = t / nph;
-    int tx = r % p.tiles_x;
-    r /= p.tiles_x;
-    int ty = r % p.tiles_y;
-    n = r / p.tiles_y;
+    const bool t4 = p.mode == MODE_T;
+    phase = t4 ? t & 3 : 0;
+    const uint32_t r = t4 ? (uint32_t)t >> 2 : (uint32_t)t;
+    const uint32_t r1 = p.fdx.div(r), r2 = p.fdy.div(r1);
+    const int tx = (int)(r - r1 * (uint32_t)p.tiles_x), ty = (int)(r1 - r2 * (uint32_t)p.tiles_y);
+    n = (int)r2;
     y0 = ty << p.th_log;
     x0 = p.kxf ? tx * kKxfTile : tx << p.tw_log;
 }
@@ -1004,7 +1025,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
                             const float z = __uint_as_float(r[j]) + __ldg(p.bias + j);
-                            const float res = 2.f / (1.f + expf(-z)) - 1.f;
+                            // (1 + e^-z >= 1: the fast reciprocal division is within 2 ulp)
+                            const float res = __fdividef(2.f, 1.f + expf(-z)) - 1.f;
                             const float ibv = ibt ? ibt[(ox - x0) * 3 + j] : __ldg(p.epi.ib + q * 3 + j);
                             o[j] = fminf(fmaxf(ibv + res, 0.f), 1.f);
                         }
@@ -1709,6 +1731,8 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     p.th_log = s.th_log; p.tw_log = s.tw_log;
     p.tiles_y = ceil_div(p.gh, 1 << s.th_log);
     p.tiles_x = kxf ? ceil_div(p.gw, kKxfTile) : ceil_div(p.gw, 1 << s.tw_log);
+    p.fdx = FastDiv((uint32_t)p.tiles_x);
+    p.fdy = FastDiv((uint32_t)p.tiles_y);
     p.kxf = kxf ? 1 : 0;
     long long tiles = (long long)N * p.tiles_y * p.tiles_x * (p.mode == MODE_T ? 4 : 1);
     if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
