@@ -72,6 +72,8 @@ struct TcParams {
     int th_log, tw_log;     // tile = (1 << th_log) x (1 << tw_log) = 128 pixels
     int tiles_y, tiles_x, num_tiles;
     FastDiv fdx, fdy;       // division by tiles_x, tiles_y
+    FastDiv fdco;           // division by co (the phase of an all-phase transposed conv's column)
+    int nck_log;            // log2 of the channel blocks per tap (a power of two)
     int nck;                // channel blocks per tap
     int taps;               // 9 (conv, MODE_T3) or 4 (convT phase)
     int in_cs, in_coff;     // input pixel stride / channel offset (elements)
@@ -478,7 +480,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 // boxes in K order (ky, channel block)
                 const int ngroups = 3 * p.nck;
                 for (int grp = 0; grp < ngroups && !stop; ++grp) {
-                        const int ky = grp / p.nck, c = grp - ky * p.nck;
+                        const int ky = grp >> p.nck_log, c = grp & (p.nck - 1);
                         if (!wait_bar(ptx::smem_u32(&bars->empty[sa]), pa ^ 1, abort, p.err, 1)) { stop = true; break; }
                         uint32_t fa = ptx::smem_u32(&bars->full[sa]);
                         ptx::mbar_arrive_expect_tx(fa, A_BYTES);
@@ -522,13 +524,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 tile_coords(p, t, ph, n, y0, x0);
                 for (int kb = 0; kb < kblocks; ++kb) {
                     if (!wait_bar(ptx::smem_u32(&bars->empty[stage]), phase_bit ^ 1, abort, p.err, 1)) break;
-                    int tap = kb / p.nck, c0 = (kb - tap * p.nck) * CK;
+                    int tap = kb >> p.nck_log, c0 = (kb & (p.nck - 1)) * CK;
                     uint32_t fb = ptx::smem_u32(&bars->full[stage]);
                     ptx::mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES);
                     uint32_t da = ptx::smem_u32(sA + stage * A_STRIDE), db = ptx::smem_u32(sB + stage * B_STRIDE);
                     if (p.mode == MODE_S1 || p.mode == MODE_T3) {
                         // K order (ky, channel block, kx): the same as the halo path
-                        const int ky = kb / (3 * p.nck), r = kb - ky * 3 * p.nck, kx = r % 3;
+                        const int ky = (kb >> p.nck_log) / 3, r = kb - ((ky * 3) << p.nck_log), kx = r % 3;
                         c0 = (r / 3) * CK;
                         tap = ky * 3 + kx;
                         ptx::tma_load_4d(da, &tmA, fb, p.in_coff + c0, x0 + kx - 1 + ip, y0 + ky - 1 + ip, n);
@@ -845,7 +847,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             kst[(pj >> 1) * 300 + (2 * (lane - 1) + (pj & 1)) * 5 + co] =
                                 resid_value(nb, col, v[j], r_sc[co], r_bias[co]);
                         } else if (p.mode == MODE_T3) {
-                            const int pj = col / p.co, co = col - pj * p.co;
+                            const int pj = (int)p.fdco.div((uint32_t)col), co = col - pj * p.co;
                             epi_elem(p, n, 2 * y0 + (pj >> 1), 2 * kgx + (pj & 1), co, v[j]);
                         } else {
                             epi_elem(p, n, y0, kgx, col, v[j]);
@@ -986,8 +988,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         if (p.mode == MODE_T)
                             ptx::tma_store_5d(&tmC, sbuf, (ph & 1) * p.out_cs + p.out_coff + k0, bx, ph >> 1, by, n);
                         else if (t3) // phase k0 / C_out: output row parity >> 1, column parity & 1
-                            ptx::tma_store_5d(&tmC, sbuf, ((k0 / p.co) & 1) * p.out_cs + p.out_coff, bx,
-                                              (k0 / p.co) >> 1, by, n);
+                            ptx::tma_store_5d(&tmC, sbuf, ((int)p.fdco.div((uint32_t)k0) & 1) * p.out_cs + p.out_coff,
+                                              bx, (int)p.fdco.div((uint32_t)k0) >> 1, by, n);
                         else
                             ptx::tma_store_4d(&tmC, sbuf, p.out_coff + k0, bx, by, n);
                         ptx::bulk_commit();
@@ -1012,7 +1014,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 if (!valid || c >= ncols) continue;
                 // output pixel and channel of column c (a chunk never straddles a
                 // phase when C_out is a multiple of 16)
-                int cph = p.mode == MODE_T3 ? c / p.co : ph;
+                int cph = p.mode == MODE_T3 ? (int)p.fdco.div((uint32_t)c) : ph;
                 int co0 = p.mode == MODE_T3 ? c - cph * p.co : c;
                 int oy = gy, ox = gx;
                 if (p.mode == MODE_T || p.mode == MODE_T3) { oy = 2 * gy + (cph >> 1); ox = 2 * gx + (cph & 1); }
@@ -1070,7 +1072,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         int col = c + j, pj = cph, co = col;
                         int yy = oy, xx = ox;
                         if (p.mode == MODE_T3) {
-                            pj = col / p.co;
+                            pj = (int)p.fdco.div((uint32_t)col);
                             co = col - pj * p.co;
                             yy = 2 * gy + (pj >> 1);
                             xx = 2 * gx + (pj & 1);
@@ -1738,9 +1740,13 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
     if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
     p.num_tiles = (int)tiles;
     p.nck = cip / ck;
+    p.nck_log = 0;
+    while ((1 << p.nck_log) < p.nck) ++p.nck_log;
+    if ((1 << p.nck_log) != p.nck) { set_error("layer %s: channel blocks per tap not a power of two", L.name); return FVV_ESHAPE; }
     p.taps = p.mode == MODE_T ? 4 : 9;
     p.in_cs = in_cs; p.in_coff = in_coff;
     p.co = L.co; p.relu = L.relu; p.out_f32 = out_f32 ? 1 : 0;
+    p.fdco = FastDiv((uint32_t)L.co);
     p.acc_scale = f8 ? h->q_acc[li] : nullptr;
     p.out_fp8 = f8_on && feeds_fp8(li) && !out_f32 ? 1 : 0;
     p.out_q = h->q_out[li];
