@@ -22,8 +22,8 @@
 //
 // Warps: 0 loads the resident weights (TMA), 1 allocates TMEM and issues the MMAs, 2-5 are
 // the epilogue (TMEM lane quarters), 6 .. 6 + 8 NG - 1 are NG loader groups of 8 warps;
-// group g computes the input rows k = g, g + NG, ... of the CTA's row sequence, one pixel
-// per thread, into slot k mod kSlots.
+// group g computes the new input rows of the CTA's tiles g, g + NG, ... (one pixel per
+// thread and row) into a ring of row slots.
 #include <cuda.h>
 #include <cuda_fp8.h>
 
