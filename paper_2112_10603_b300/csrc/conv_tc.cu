@@ -195,21 +195,29 @@ __device__ __forceinline__ float resid_value(const float (&nb)[3][3][5], int col
                ly * ((1.f - lx) * nb[py + 1][px][co] + lx * nb[py + 1][px + 1][co]);
     return acc * sc + bias + up * (co < 4 ? 2.f : 1.f);
 }
-__device__ __forceinline__ float resid_value(const TcParams &p, const float (&nb)[3][3][5], int col, float acc) {
-    const int co = col % 5;
-    return resid_value(nb, col, acc, p.acc_scale ? __ldg(p.acc_scale + co) : 1.f, __ldg(p.bias + co));
+// Bias and dequantisation scale (1 without) of output channel co: from the copies staged in
+// shared memory (SB: sb, ss are their shared addresses), or from global memory.
+template <bool SB> __device__ __forceinline__ float bias_of(const TcParams &p, uint32_t sb, int co) {
+    return SB ? ptx::lds_f32(sb + 4 * co) : __ldg(p.bias + co);
 }
-__device__ __forceinline__ void resid_store(const TcParams &p, const float (&nb)[3][3][5], int n, int gy, int gx,
-                                            int col, float acc) {
+template <bool SB> __device__ __forceinline__ float scale_of(const TcParams &p, uint32_t ss, int co) {
+    return SB ? ptx::lds_f32(ss + 4 * co) : (p.acc_scale ? __ldg(p.acc_scale + co) : 1.f);
+}
+template <bool SB>
+__device__ __forceinline__ void resid_store(const TcParams &p, uint32_t sb, uint32_t ss, const float (&nb)[3][3][5],
+                                            int n, int gy, int gx, int col, float acc) {
     const int pj = col / 5, co = col % 5, py = pj >> 1, px = pj & 1;
     size_t pix = ((size_t)n * p.out_h + 2 * gy + py) * p.out_w + 2 * gx + px;
-    ((float *)p.out)[pix * p.out_cs + p.out_coff + co] = resid_value(p, nb, col, acc);
+    ((float *)p.out)[pix * p.out_cs + p.out_coff + co] =
+        resid_value(nb, col, acc, scale_of<SB>(p, ss, co), bias_of<SB>(p, sb, co));
 }
 
 // One output element of the epilogue (scalar path): bias, ReLU, then store, or
 // the fused Eq. 2 update.
-__device__ __forceinline__ void epi_elem(const TcParams &p, int n, int oy, int ox, int co, float acc) {
-    float x = acc * (p.acc_scale ? __ldg(p.acc_scale + co) : 1.f) + __ldg(p.bias + co);
+template <bool SB>
+__device__ __forceinline__ void epi_elem(const TcParams &p, uint32_t sb, uint32_t ss, int n, int oy, int ox, int co,
+                                         float acc) {
+    float x = acc * scale_of<SB>(p, ss, co) + bias_of<SB>(p, sb, co);
     if (p.relu) x = fmaxf(x, 0.f);
     if (p.amax) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(fabsf(x)));
     size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
@@ -312,6 +320,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     static_assert(STAGES + 1 + NIB <= 16, "barrier slots");
     float *const ibs = (float *)(stg + (TS ? 4 * NSB * STG_BYTES : KST_BYTES));
     Bars *bars = (Bars *)(stg + (TS ? 4 * NSB * STG_BYTES : KST_BYTES) + NIB * IB_SLOT);
+    // the layer's biases and dequantisation scales (1 without) for output channels co < BN,
+    // staged once per CTA for the TMA-store epilogue of the one- and two-CTA kernels
+    // (measured: 2-3 % faster there; the four-CTA kernels, capped at 80 registers, spilled
+    // with it, and the per-thread-store epilogue of the all-phase d3 got slower)
+    constexpr bool SB = TS && CTAS <= 2;
+    float *const sbias_p = (float *)(bars + 1);
     volatile int *abort = &bars->abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -339,6 +353,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
         if (TS && p.tma_store) ptx::prefetch_tmap(&tmC);
+    }
+    for (int i = threadIdx.x; SB && i < BN; i += kThreads) {
+        sbias_p[i] = i < p.co ? __ldg(p.bias + i) : 0.f;
+        sbias_p[BN + i] = i < p.co && p.acc_scale ? __ldg(p.acc_scale + i) : 1.f;
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), TMEM_COLS);
@@ -773,6 +791,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
+        const uint32_t sbias = ptx::smem_u32(bars + 1), sscale = sbias + 4 * BN; // staged biases, scales
         const int q = warp & 3;           // TMEM lane quarter this warp may access
         const int row = q * 32 + lane;    // tile row = accumulator lane
         int acc = 0;
@@ -848,9 +867,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 resid_value(nb, col, v[j], r_sc[co], r_bias[co]);
                         } else if (p.mode == MODE_T3) {
                             const int pj = (int)p.fdco.div((uint32_t)col), co = col - pj * p.co;
-                            epi_elem(p, n, 2 * y0 + (pj >> 1), 2 * kgx + (pj & 1), co, v[j]);
+                            epi_elem<SB>(p, sbias, sscale, n, 2 * y0 + (pj >> 1), 2 * kgx + (pj & 1), co, v[j]);
                         } else {
-                            epi_elem(p, n, y0, kgx, col, v[j]);
+                            epi_elem<SB>(p, sbias, sscale, n, y0, kgx, col, v[j]);
                         }
                     }
                 }
@@ -884,7 +903,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ptx::tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        if (c + j < 20 && valid) resid_store(p, nb, n, gy, gx, c + j, __uint_as_float(r[j]));
+                        if (c + j < 20 && valid) resid_store<SB>(p, sbias, sscale, nb, n, gy, gx, c + j, __uint_as_float(r[j]));
                 }
             } else {
             if (!wait_bar(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
@@ -931,8 +950,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         float vmax = 0.f;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            float sc = p.acc_scale ? __ldg(p.acc_scale + cc + j) : 1.f;
-                            float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + cc + j);
+                            float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, cc + j) +
+                                      bias_of<SB>(p, sbias, cc + j);
                             v[j] = p.relu ? fmaxf(a, 0.f) : a;
                             vmax = fmaxf(vmax, fabsf(v[j]));
                         }
@@ -1026,7 +1045,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         float *o = out_final + (((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3;
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
-                            const float z = __uint_as_float(r[j]) + __ldg(p.bias + j);
+                            const float z = __uint_as_float(r[j]) + bias_of<SB>(p, sbias, j);
                             // (1 + e^-z >= 1: the fast reciprocal division is within 2 ulp)
                             const float res = __fdividef(2.f, 1.f + expf(-z)) - 1.f;
                             const float ibv = ibt ? ibt[(ox - x0) * 3 + j] : __ldg(p.epi.ib + q * 3 + j);
@@ -1040,8 +1059,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     float vmax = 0.f;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        float sc = p.acc_scale ? __ldg(p.acc_scale + co0 + j) : 1.f;
-                        float a = __uint_as_float(r[j]) * sc + __ldg(p.bias + co0 + j);
+                        float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, co0 + j) +
+                                  bias_of<SB>(p, sbias, co0 + j);
                         v[j] = p.relu ? fmaxf(a, 0.f) : a;
                         vmax = fmaxf(vmax, fabsf(v[j]));
                     }
@@ -1077,7 +1096,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             yy = 2 * gy + (pj >> 1);
                             xx = 2 * gx + (pj & 1);
                         }
-                        epi_elem(p, n, yy, xx, co, __uint_as_float(r[j]));
+                        epi_elem<SB>(p, sbias, sscale, n, yy, xx, co, __uint_as_float(r[j]));
                     }
                 }
             }
@@ -1186,7 +1205,7 @@ template <int BN, int CK, int MT, int F8 = 0, int TS = 0> struct Cfg {
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 3 + !TS ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for((512 / TMEM_COLS) < 4 ? (512 / TMEM_COLS) : 4);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * (A + B) + STG + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * (A + B) + STG + sizeof(Bars) + 8 * BN + 1024;
     static_assert(STAGES >= 2 && CTAS * TMEM_COLS <= 512, "tensor-core config");
 };
 
@@ -1233,7 +1252,7 @@ template <int BN, int TS, int MT = 1> struct HaloCfg {
                                        : (BN >= 256 ? 2 : (BN >= 128 ? 3 : (BN >= 64 ? 4 : 3)));
     static constexpr int STAGES_B = TS ? (BN >= 256 ? 4 : (BN >= 128 ? 2 : (BN >= 64 ? 3 : 4)))
                                        : (BN >= 256 ? 5 : (BN >= 128 ? 3 : 4));
-    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * A + (size_t)STAGES_B * B + STG + sizeof(Bars) + 8 * BN + 1024;
     static_assert(CTAS * SMEM <= kSmemBudget + 8 * 1024 && CTAS * TMEM_COLS <= 512 && STAGES >= 2 && STAGES_B >= 2,
                   "halo config");
 };
@@ -1256,7 +1275,7 @@ template <int BN, int CK, int TS, int F8 = 0, int RES = 0> struct HaloGrpCfg {
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 2 ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for(BN <= 32 ? 4 : 2);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * G + BR + STG + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * G + BR + STG + sizeof(Bars) + 8 * BN + 1024;
     static_assert(STAGES >= 2 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "grouped halo config");
 };
 
@@ -1294,7 +1313,7 @@ template <int BN, int CK, int F8, int NCK> struct KxfCfg {
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 3 ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for(3);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * A + BR + KST + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * A + BR + KST + sizeof(Bars) + 8 * BN + 1024;
     static_assert(STAGES >= 2 && STAGES < 16 && CTAS * AccCfg<BN, 1>::TMEM_COLS <= 512, "folded-tap config");
 };
 
@@ -1389,7 +1408,7 @@ template <int BN, int CK, int TS> struct S2hCfg {
     static constexpr int ctas_for(int c) { return c > 1 && stages_for(c) < 4 ? ctas_for(c - 1) : c; }
     static constexpr int CTAS = ctas_for(512 / TMEM_COLS < 4 ? 512 / TMEM_COLS : 4);
     static constexpr int STAGES = stages_for(CTAS) > 8 ? 8 : stages_for(CTAS);
-    static constexpr size_t SMEM = (size_t)STAGES * A + BR + STG + sizeof(Bars) + 1024;
+    static constexpr size_t SMEM = (size_t)STAGES * A + BR + STG + sizeof(Bars) + 8 * BN + 1024;
     static_assert(STAGES >= 3 && CTAS * TMEM_COLS <= 512, "stride-2 halo config");
 };
 
