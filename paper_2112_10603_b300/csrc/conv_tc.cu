@@ -807,8 +807,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             r_bias[k] = KXF && p.epi.mode == EPI_RESID ? __ldg(p.bias + k) : 0.f;
             r_sc[k] = KXF && p.epi.mode == EPI_RESID && p.acc_scale ? __ldg(p.acc_scale + k) : 1.f;
         }
-        // fused network output (N = 16 tiles): the cropped output buffer
+        // fused network output (N = 16 tiles): the cropped output buffer and the 3 biases
         float *const out_final = BN == 16 && p.epi.mode == EPI_OUTPUT ? *p.epi.final_out_ref : nullptr;
+        float obias[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) obias[j] = BN == 16 && p.epi.mode == EPI_OUTPUT ? __ldg(p.bias + j) : 0.f;
         long long tk = -1; // this CTA's tile count (I_blend ring slot / phase)
         for (int t = blockIdx.x; t < num_tiles && !*abort; t += gridDim.x) {
             ++tk;
@@ -1045,7 +1048,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         float *o = out_final + (((size_t)n * p.epi.crop_h + oy) * p.epi.crop_w + ox) * 3;
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
-                            const float z = __uint_as_float(r[j]) + bias_of<SB>(p, sbias, j);
+                            const float z = __uint_as_float(r[j]) + obias[j];
                             // (1 + e^-z >= 1: the fast reciprocal division is within 2 ulp)
                             const float res = __fdividef(2.f, 1.f + expf(-z)) - 1.f;
                             const float ibv = ibt ? ibt[(ox - x0) * 3 + j] : __ldg(p.epi.ib + q * 3 + j);
