@@ -212,3 +212,27 @@ def test_folded_t1_network_matches_plain_t1(torch_cuda, tmp_path):
         assert d.max() < 0.05, (s, float(d.max()))
     d = np.abs(folded - plain)
     assert d.max() < 0.05 and d.mean() < 1e-3, (float(d.max()), float(d.mean()))
+
+
+@pytest.mark.parametrize("H,W,nv", [(72, 400, 3), (200, 136, 2)])
+def test_stage_input_in_c0_loader_bitwise(torch_cuda, tmp_path, H, W, nv):
+    """VIB1/VIB2 c0 with the stage input computed by its loader warps (never stored)
+    against the stage-input kernel followed by the per-tap c0 (a tile width forced for
+    the two c0 layers in the tile cache turns the fusion off): the same bits, on ragged
+    column strips (400 wide: VIB2 c0 outputs 200 = 126 + 74 per row), several views and
+    tile ranges that cross strips and views."""
+    torch = torch_cuda
+    left, right = pair(31, H, W, 9.0)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.2, 0.5, 0.9][:nv]
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=nv)
+    fused = it.run(L, R, ts).cpu().numpy()
+    flows = [it.peek(f"vib{s}").copy() for s in range(3)]
+    cache = tmp_path / "c0.json"
+    cache.write_text(json.dumps({f"{H}x{W} n{nv} p{fvv.FVV_BF16}": {"vib1.c0": 7, "vib2.c0": 7}}))
+    it.autotune(nv, str(cache))
+    apart = it.run(L, R, ts).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    for s in range(3):
+        np.testing.assert_array_equal(it.peek(f"vib{s}"), flows[s])
+    np.testing.assert_array_equal(apart, fused)
