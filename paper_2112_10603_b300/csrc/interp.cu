@@ -184,18 +184,31 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
     // when the caller (the server) knows the frames are those of the handle's last run.
     if (!h->skip_cams)
         FVV_TRY(launch_prep_cams(h->d_cams, n_cams, nc_dev, h->H, h->W, Hp, Wp, h->img0, h->img1, h->img2, st));
+    // ContextNet shares no buffer with the VIBlocks (its own scratch and outputs; they meet
+    // only at RefineNet's context warps), so it runs on a second stream beside them and
+    // fills the SMs their small kernels leave idle.  Not while profiling (per-layer times
+    // would overlap) nor in circular mode (every tensor-core conv stages its input in the
+    // one wrapped-border buffer).
+    const bool fork = !h->skip_cams && !circ && !h->profiling;
+    cudaStream_t sc = st;
+    if (fork) {
+        FVV_CHECK_CUDA(cudaEventRecord(h->ev_fork, st));
+        FVV_CHECK_CUDA(cudaStreamWaitEvent(h->ctx_stream, h->ev_fork, 0));
+        sc = h->ctx_stream;
+    }
     if (!h->skip_cams) {
         int hh = Hp, ww = Wp;
         const void *cur = h->img0; // FP32 frame: the 3-channel first layer runs on the SIMT kernel
         int cur_cs = 4;
         const int C[4] = {16, 32, 64, 128};
         for (int k = 0; k < 4; ++k) {
-            FVV_TRY(conv(h, kCtx + 2 * k, cur, cur_cs, 0, n_cams, hh, ww, h->ctxt, C[k], 0, false, st));
+            FVV_TRY(conv(h, kCtx + 2 * k, cur, cur_cs, 0, n_cams, hh, ww, h->ctxt, C[k], 0, false, sc));
             hh /= 2; ww /= 2;
-            FVV_TRY(conv(h, kCtx + 2 * k + 1, h->ctxt, C[k], 0, n_cams, hh, ww, h->ctx[k], C[k], 0, false, st));
+            FVV_TRY(conv(h, kCtx + 2 * k + 1, h->ctxt, C[k], 0, n_cams, hh, ww, h->ctx[k], C[k], 0, false, sc));
             cur = h->ctx[k]; cur_cs = C[k];
         }
     }
+    if (fork) FVV_CHECK_CUDA(cudaEventRecord(h->ev_join, sc));
     // a2-a4: VIBlocks
     for (int s = 0; s < 3; ++s) {
         int hs = Hp >> (2 - s), ws = Wp >> (2 - s);
@@ -230,6 +243,7 @@ template <typename T> static int forward_t(fvv_interp *h, int n_cams, int nv, cu
             if (s > 0) FVV_TRY(launch_residual(h->fm[s - 1], h->fm[s], nv, nv_dev, hs, ws, circ, st));
         }
     }
+    if (fork) FVV_CHECK_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0)); // ContextNet done
     // a5: final warp + blend
     FVV_TRY(launch_final_blend<T>(h->img0, h->fm[2], vt, nv, Hp, Wp, circ, U[0], cu0, h->ib, st));
     // a6 + a7: RefineNet with context warps.  Level tensors (channel slots):
@@ -354,6 +368,9 @@ static int create_impl(fvv_interp *h, const float *blob) {
         FVV_TRY(dalloc(h, &h->cpad, h->cpad_bytes));
     }
     FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    FVV_CHECK_CUDA(cudaStreamCreateWithFlags(&h->ctx_stream, cudaStreamNonBlocking));
+    FVV_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    FVV_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     FVV_CHECK_CUDA(cudaMemset(h->d_err, 0, 64));
     FVV_CHECK_CUDA(cudaMallocHost(&h->h_stage, V * 12 + (C + 1) * sizeof(float *) + 64));
     FVV_CHECK_CUDA(cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming));
@@ -967,6 +984,9 @@ void fvv_interp_destroy(fvv_interp *h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->ctx_stream) cudaStreamDestroy(h->ctx_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (auto &sl : h->hs)
         for (cudaEvent_t e : {sl.in_ready, sl.fwd_done, sl.out_done})
             if (e) cudaEventDestroy(e);

@@ -108,6 +108,10 @@ struct fvv_interp {
     size_t cpad_bytes = 0;
     long long graph_captures = 0;
     cudaStream_t cap_stream = nullptr;
+    // ContextNet runs on its own stream beside the VIBlocks (forked after the frame pyramid,
+    // joined before RefineNet's context warps); in a captured graph: two branches
+    cudaStream_t ctx_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // tile rectangle per layer: log2 of the tile width (-1: fewest-tiles default);
     // tile_force >= 0 overrides every layer (used while autotuning)
     signed char tile_tw[fvv::kNumLayers];
