@@ -110,6 +110,18 @@ struct TcParams {
 // warp never needs another warp's rows: lanes 1..30 produce outputs, 120 per tile.
 constexpr int kKxfTile = 120;
 
+// 16 values times q as E4M3 codes (paired conversions, RNE, saturating), value j in byte j
+__device__ __forceinline__ uint4 e4m3x16(const float (&v)[16], float q) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k] * q, v[4 * k + 1] * q), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k + 2] * q, v[4 * k + 3] * q), __NV_SATFINITE, __NV_E4M3);
+        w[k] = lo | (hi << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
 __device__ __forceinline__ uint8_t to_e4m3(float v) {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
@@ -950,23 +962,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     // (output channels cc .. cc + 15)
                     auto stage16 = [&](int c, int cc, const uint32_t(&r)[16]) {
                         float v[16];
-                        float vmax = 0.f;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, cc + j) +
                                       bias_of<SB>(p, sbias, cc + j);
                             v[j] = p.relu ? fmaxf(a, 0.f) : a;
-                            vmax = fmaxf(vmax, fabsf(v[j]));
                         }
-                        if (p.amax && valid) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
+                        if (p.amax && valid) { // calibration only
+                            float vmax = 0.f;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) vmax = fmaxf(vmax, fabsf(v[j]));
+                            atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
+                        }
                         const uint32_t a0 = sbuf + lane * chb + (c - k0) * oes;
                         if (p.out_fp8) {
-                            uint8_t q8[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) q8[j] = to_e4m3(v[j] * p.out_q);
-                            uint4 w;
-                            memcpy(&w, q8, 16);
-                            ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), w);
+                            ptx::st_shared_v4(a0 ^ (((a0 >> 7) & swm) << 4), e4m3x16(v, p.out_q));
                         } else {
                             __nv_bfloat162 h[8];
 #pragma unroll
@@ -1059,23 +1069,22 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co) {
                     float v[16];
-                    float vmax = 0.f;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, co0 + j) +
                                   bias_of<SB>(p, sbias, co0 + j);
                         v[j] = p.relu ? fmaxf(a, 0.f) : a;
-                        vmax = fmaxf(vmax, fabsf(v[j]));
                     }
-                    if (p.amax) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
+                    if (p.amax) { // calibration only
+                        float vmax = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) vmax = fmaxf(vmax, fabsf(v[j]));
+                        atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
+                    }
                     size_t pix = ((size_t)n * p.out_h + oy) * p.out_w + ox;
                     if (p.out_fp8) {
-                        uint8_t q8[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) q8[j] = to_e4m3(v[j] * p.out_q);
-                        uint4 w;
-                        memcpy(&w, q8, 16);
-                        *reinterpret_cast<uint4 *>((uint8_t *)p.out + pix * p.out_cs + p.out_coff + co0) = w;
+                        *reinterpret_cast<uint4 *>((uint8_t *)p.out + pix * p.out_cs + p.out_coff + co0) =
+                            e4m3x16(v, p.out_q);
                     } else {
                         __nv_bfloat162 h[8];
 #pragma unroll

@@ -317,13 +317,18 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
                         for (int j = 0; j < 16; ++j) vmax = fmaxf(vmax, v[j]);
                     }
                     if (p.out_fp8) {
-                        uint8_t q8[16];
+                        // E4M3 codes of v x out_q, value j in byte j (paired conversions)
+                        uint32_t w[4];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            q8[j] = (uint8_t)__nv_cvt_float_to_fp8(v[j] * p.out_q, __NV_SATFINITE, __NV_E4M3);
-                        uint4 u;
-                        memcpy(&u, q8, 16);
-                        ptx::st_shared_v4(stg_s + lane * 128 + (((cb >> 4) ^ (lane & 7)) << 4), u);
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t lo = __nv_cvt_float2_to_fp8x2(
+                                make_float2(v[4 * k] * p.out_q, v[4 * k + 1] * p.out_q), __NV_SATFINITE, __NV_E4M3);
+                            const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                                make_float2(v[4 * k + 2] * p.out_q, v[4 * k + 3] * p.out_q), __NV_SATFINITE, __NV_E4M3);
+                            w[k] = lo | (hi << 16);
+                        }
+                        ptx::st_shared_v4(stg_s + lane * 128 + (((cb >> 4) ^ (lane & 7)) << 4),
+                                          make_uint4(w[0], w[1], w[2], w[3]));
                     } else {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
