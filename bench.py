@@ -44,7 +44,7 @@ FP32_FFMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 
 # profiles/conv_tc_fp8_halo_vib2_m1_1080p_7views.md); a launch's traffic is its views'
 # activations, so other view counts scale it by views / 7.  None: the kernel changed
 # since the last capture.  Refresh when the kernel changes.
-TRAFFIC_VIB2_M = {"bf16": 469_190_400 + 427_399_424, "fp8": 234_652_928 + 194_028_032}
+TRAFFIC_VIB2_M = {"bf16": 469_219_840 + 426_995_456, "fp8": 234_663_936 + 194_137_856}
 TRAFFIC_VIEWS = 7
 
 
