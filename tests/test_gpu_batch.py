@@ -6,7 +6,9 @@
   same K-loop order whatever the tile) and the JSON cache round-trips;
 * a rig instant with uneven per-pair view counts (one batch) equals per-pair runs;
 * every view of such a rig instant matches the FP64 oracle's view of its pair:
-  FP32 path max |err| <= 1e-4, BF16 path PSNR >= 45 dB.
+  FP32 path max |err| <= 1e-4, BF16 path PSNR >= 45 dB;
+* ContextNet on its own stream beside the VIBlocks (the default) gives the same bits as
+  the whole forward on one stream (profiling mode runs it so).
 """
 import json
 
@@ -137,3 +139,23 @@ def test_bucket_graphs_replay_any_view_mix(torch_cuda, precision):
     fvv.fvv_interp_status(g.h)
     assert g.graph_captures <= 5, g.graph_captures      # buckets 1, 2, 4, 8, 16
     assert d.graph_captures == 0
+
+
+@pytest.mark.parametrize("precision", [fvv.FVV_FP32, fvv.FVV_BF16])
+def test_contextnet_stream_fork_keeps_bits(torch_cuda, precision):
+    torch = torch_cuda
+    H, W = 136, 200
+    left, right = pair(41, H, W, 7.0)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.25, 0.75]
+    for graphs in (1, 0):
+        it = fvv.Interpolator(blob(), H, W, precision=precision, max_views=2, graphs=graphs)
+        forked = it.run(L, R, ts).cpu().numpy()
+        fvv.fvv_interp_profile(it.h, True)          # one stream, events around every conv
+        serial = it.run(L, R, ts).cpu().numpy()
+        fvv.fvv_interp_profile(it.h, False)
+        again = it.run(L, R, ts).cpu().numpy()
+        fvv.fvv_interp_status(it.h)
+        np.testing.assert_array_equal(serial, forked)
+        np.testing.assert_array_equal(again, forked)
+        it.close()
