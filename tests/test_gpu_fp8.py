@@ -15,7 +15,13 @@ from synth import scene, weights
 from tests.gpu_common import blob, oracle_view, pair, psnr
 
 pytestmark = pytest.mark.gpu
-PSNR_FP8_FLOOR = 30.0     # dB; the measured value is printed (target 38 dB)
+# 256x256, seed 1: 34.6-34.8 dB over three scenes and five calibration sets.  The E4M3
+# rounding of weights and activations (relative step 2^-3) leaves 10-13% RMS relative
+# error in the stage flows at every size; the 256x256 scenes have about 7x the per-pixel
+# image gradient of the 1080p ones, so the same flow error costs ~6 dB more there
+# (1080p: 40.7 dB, held to the 38 dB target below).
+PSNR_FP8_FLOOR = 34.0
+FLOW_REL_ERR_MAX = 0.14   # RMS flow error / RMS flow, each stage s of Eq. 2
 
 
 @pytest.fixture(scope="module")
@@ -120,7 +126,7 @@ def test_fp8_strided_and_transposed_layers(torch_cuda, name):
 def test_fp8_network_psnr(torch_cuda, H, W, seed, disp):
     torch = torch_cuda
     left, right = pair(seed, H, W, disp)
-    ref, _ = oracle_view(seed, H, W, disp, 0.5)
+    ref, d = oracle_view(seed, H, W, disp, 0.5)
     it8 = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=3)
     fvv.fvv_calibrate_fp8(it8.h, _calib_frames(torch, H, W), 2)
     it16 = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=1)
@@ -131,12 +137,18 @@ def test_fp8_network_psnr(torch_cuda, H, W, seed, disp):
     print(f"FP8 {H}x{W}: PSNR {p8:.2f} dB vs FP64, {p816:.2f} dB vs BF16, max err {np.abs(o8 - ref).max():.4f}")
     assert np.isfinite(o8).all() and o8.min() >= 0 and o8.max() <= 1
     assert p8 >= PSNR_FP8_FLOOR, p8
+    for s in range(3):
+        g, r = it8.peek(f"vib{s}")[..., :4], d[f"vib{s}"][..., :4]
+        rel = np.sqrt(((g - r) ** 2).mean() / (r ** 2).mean())
+        print(f"  stage {s}: flow RMS relative error {rel:.3f}")
+        assert rel <= FLOW_REL_ERR_MAX, (s, rel)
 
 
 def test_fp8_1080p_fifteen_views(torch_cuda):
     """1920x1080, 15 views at t = k/16, calibration on 8 held-out scenes (seeds
-    100-107): the midpoint view reaches 38 dB against the FP64 oracle, every view is
-    finite and in [0, 1], and each view equals the same view computed alone."""
+    100-107): the midpoint view reaches 38 dB against the FP64 oracle with its stage
+    flows within the same relative error as at 256x256, every view is finite and in
+    [0, 1], and each view equals the same view computed alone."""
     torch = torch_cuda
     H, W = 1080, 1920
     it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=15)
@@ -147,9 +159,13 @@ def test_fp8_1080p_fifteen_views(torch_cuda):
     out = it.run(L, R, ts).cpu().numpy()
     fvv.fvv_interp_status(it.h)
     assert np.isfinite(out).all() and out.min() >= 0 and out.max() <= 1
-    ref, _ = oracle_view(2, H, W, 64.0, 0.5)
+    ref, d = oracle_view(2, H, W, 64.0, 0.5)
     p = psnr(out[7], ref)
     print(f"FP8 1080p t=0.5 (15-view batch): PSNR {p:.2f} dB")
     assert p >= 38.0, p
+    for s in range(3):
+        g, r = it.peek(f"vib{s}", view=7)[..., :4], d[f"vib{s}"][..., :4]
+        rel = np.sqrt(((g - r) ** 2).mean() / (r ** 2).mean())
+        assert rel <= FLOW_REL_ERR_MAX, (s, rel)
     alone = it.run(L, R, [ts[3]]).cpu().numpy()
     np.testing.assert_array_equal(alone[0], out[3])
