@@ -1041,7 +1041,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int c = 0; c < BN; c += 16) {
                 uint32_t r[16];
                 __syncwarp();
-                ptx::tmem_ld16(tb + c, r);
+                if (BN == 16 && p.epi.mode == EPI_OUTPUT) ptx::tmem_ld4(tb + c, r); // 3 output columns
+                else ptx::tmem_ld16(tb + c, r);
                 ptx::tmem_ld_wait();
                 if (!valid || c >= ncols) continue;
                 // output pixel and channel of column c (a chunk never straddles a
@@ -1059,8 +1060,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
                             const float z = __uint_as_float(r[j]) + obias[j];
-                            // (1 + e^-z >= 1: the fast reciprocal division is within 2 ulp)
-                            const float res = __fdividef(2.f, 1.f + expf(-z)) - 1.f;
+                            // (1 + e^-z >= 1: the fast reciprocal division is within 2 ulp;
+                            // the fast exponential adds ~2^-21 relative, far inside BF16)
+                            const float res = __fdividef(2.f, 1.f + __expf(-z)) - 1.f;
                             const float ibv = ibt ? ibt[(ox - x0) * 3 + j] : __ldg(p.epi.ib + q * 3 + j);
                             o[j] = fminf(fmaxf(ibv + res, 0.f), 1.f);
                         }
@@ -1490,6 +1492,12 @@ int dispatch(int bn, int ck, bool f8, const CUtensorMap &ma, const CUtensorMap &
 
 } // namespace
 
+// A bf16 tensor map with the swizzle of ck_bytes-wide rows, for the kernels of other files.
+int tc_encode_map(CUtensorMap *m, int rank, void *base, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
+                  const cuuint32_t *box, int ck_bytes) {
+    return encode(m, rank, base, dims, strides_bytes, box, ck_bytes);
+}
+
 // Pack every layer's weights as bf16 [G][Co_pad][Ci_pad] (G = 9 taps, or 4 phases
 // x 4 taps for the transposed conv) and build its B tensor map.
 int tc_prepare_fp8(fvv_interp *h, const float *blob);
@@ -1592,7 +1600,8 @@ int tc_prepare(fvv_interp *h, const float *blob) {
             FVV_TRY(encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, ck * 2));
             box[2] = 1;
         }
-        if (tc_kxf_layer(i)) folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
+        // (and RefineNet's output conv, whose dedicated kernel reads the folded slices)
+        if (tc_kxf_layer(i) || i == kRef + 12) folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
     }
     // folded copies allocated after every layer's own weights: the per-layer weight
     // allocations keep the addresses they have without them (the per-tap convs reload

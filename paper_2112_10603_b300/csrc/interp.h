@@ -143,6 +143,12 @@ int tc_conv(fvv_interp *h, int layer, const void *in, int in_cs, int in_coff, in
 // warped, the frames, t) computed by the loader of the block's first conv (c0) itself;
 // out: the c0 output (bf16, or E4M3 for an FP8 consumer), out_cs = 128
 bool stage_conv_layer(const fvv_interp *h, int layer);
+// RefineNet's output conv with the network output fused (csrc/out_conv.cu): whether the
+// dedicated kernel takes this call, and its launch (in: n x hp x wp x 16 bf16; ib: I_blend
+// on the padded grid; out_ref: device slot holding the cropped output pointer)
+bool out_conv_ok(const fvv_interp *h, int layer, int in_cs, int n, int hp, int wp, int crop_h, int crop_w);
+int tc_out_conv(fvv_interp *h, int layer, const void *in, int n, int hp, int wp, const float *ib,
+                float *const *out_ref, int crop_h, int crop_w, const int *n_dev, cudaStream_t st);
 int tc_stage_conv(fvv_interp *h, int layer, const float4 *imgs, const float *fm_prev, const ViewTab &vt, int nv,
                   int hs, int ws, int circ, void *out, int out_cs, cudaStream_t st);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases

@@ -18,7 +18,9 @@ column taps read it 0, 1, 2 rows in.  Checks:
   tap) for the per-phase transposed convs (the VIB t1 convs, whose column taps are
   folded into N and summed after the K loop, run on plain tiles in both);
 * the forward with t1's folded column taps matches the one with t1 on plain tiles to
-  FP32 rounding of that sum (stage flows, Eq. 2, and the views).
+  FP32 rounding of that sum (stage flows, Eq. 2, and the views); so does the forward
+  with RefineNet's output conv in its dedicated kernel (column taps folded into N,
+  two rows of a 120-pixel strip per tile) against ref.out on plain tiles.
 
 The transposed convs with C_out <= 32 (VIB t1, RefineNet d2, d3) run as one 3x3 conv
 over all four output phases (N = 4 C_out); d2's phases are stored by TMA through the
@@ -177,7 +179,8 @@ def test_halo_network_bitwise_plain_tiles(torch_cuda, tmp_path):
     key = f"{H}x{W} n2 p{fvv.FVV_BF16}"
     # t1 (folded column taps) on plain tiles, every other layer on its default tiles
     t1_plain = tmp_path / "t1.json"
-    t1_plain.write_text(json.dumps({key: {f"vib{s}.t1": 7 for s in range(3)}}))
+    # (and the output conv: its dedicated kernel folds the column taps too)
+    t1_plain.write_text(json.dumps({key: {**{f"vib{s}.t1": 7 for s in range(3)}, "ref.out": 7}}))
     it.autotune(2, str(t1_plain))
     halo = it.run(L, R, ts).cpu().numpy()
     # force every layer onto plain tiles 128 pixels wide through a tile cache entry
@@ -212,6 +215,33 @@ def test_folded_t1_network_matches_plain_t1(torch_cuda, tmp_path):
         assert d.max() < 0.05, (s, float(d.max()))
     d = np.abs(folded - plain)
     assert d.max() < 0.05 and d.mean() < 1e-3, (float(d.max()), float(d.mean()))
+
+
+@pytest.mark.parametrize("H,W,nv", [(71, 399, 2), (64, 512, 3)])
+def test_folded_output_conv_matches_plain(torch_cuda, tmp_path, H, W, nv):
+    """RefineNet's output conv in its dedicated kernel (column taps folded into N, the
+    three taps summed across TMEM lanes, two rows of a 120-pixel strip per tile) against
+    the generic tensor-core conv on plain tiles (a tile width forced for ref.out in the
+    tile cache), the rest of the network unchanged: the two differ only in the FP32 order
+    of the nine taps' sums, so every intermediate is the same and the views agree to far
+    below BF16 noise.  Odd crop height (the last row pair half outside), odd crop width
+    (scalar stores), ragged last strips."""
+    torch = torch_cuda
+    left, right = pair(29, H, W, 8.0)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.25, 0.5, 0.75][:nv]
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=nv)
+    folded = it.run(L, R, ts).cpu().numpy()
+    blend = it.peek("blend").copy()
+    cache = tmp_path / "out.json"
+    cache.write_text(json.dumps({f"{H}x{W} n{nv} p{fvv.FVV_BF16}": {"ref.out": 7}}))
+    it.autotune(nv, str(cache))
+    plain = it.run(L, R, ts).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    np.testing.assert_array_equal(it.peek("blend"), blend)
+    assert folded.shape == (nv, H, W, 3) and np.isfinite(folded).all()
+    d = np.abs(folded - plain)
+    assert d.max() <= 2e-5, float(d.max())
 
 
 @pytest.mark.parametrize("H,W,nv", [(72, 400, 3), (200, 136, 2)])
