@@ -1600,8 +1600,9 @@ int tc_prepare(fvv_interp *h, const float *blob) {
             FVV_TRY(encode((CUtensorMap *)tw.map3, 3, tw.w, dims, strides, box, ck * 2));
             box[2] = 1;
         }
-        // (and RefineNet's output conv, whose dedicated kernel reads the folded slices)
-        if (tc_kxf_layer(i) || i == kRef + 12) folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
+        // (and RefineNet's output conv and d3, whose dedicated kernels read the folded slices)
+        if (tc_kxf_layer(i) || i == kRef + 12 || i == kRef + 11)
+            folds.push_back({i, std::move(pk), cop, cip, t3 ? 4 * L.co : L.co, ck});
     }
     // folded copies allocated after every layer's own weights: the per-layer weight
     // allocations keep the addresses they have without them (the per-tap convs reload

@@ -149,6 +149,13 @@ bool stage_conv_layer(const fvv_interp *h, int layer);
 bool out_conv_ok(const fvv_interp *h, int layer, int in_cs, int n, int hp, int wp, int crop_h, int crop_w);
 int tc_out_conv(fvv_interp *h, int layer, const void *in, int n, int hp, int wp, const float *ib,
                 float *const *out_ref, int crop_h, int crop_w, const int *n_dev, cudaStream_t st);
+// RefineNet d3 (all-phase transposed conv 64 -> 16, column taps folded into N;
+// csrc/convt_fold.cu): whether the dedicated kernel takes this call, and its launch
+// (in: n x hin x win pixels of in_cs bf16 channels, the first 64 used; out: bf16,
+// n x 2 hin x 2 win x 16)
+bool convt_fold_ok(const fvv_interp *h, int layer, int in_cs, int in_coff, int out_cs, int out_coff, bool out_f32);
+int tc_convt_fold(fvv_interp *h, int layer, const void *in, int in_cs, int n, int hin, int win, void *out,
+                  const int *n_dev, cudaStream_t st);
 int tc_stage_conv(fvv_interp *h, int layer, const float4 *imgs, const float *fm_prev, const ViewTab &vt, int nv,
                   int hs, int ws, int circ, void *out, int out_cs, cudaStream_t st);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases

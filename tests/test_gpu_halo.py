@@ -179,8 +179,8 @@ def test_halo_network_bitwise_plain_tiles(torch_cuda, tmp_path):
     key = f"{H}x{W} n2 p{fvv.FVV_BF16}"
     # t1 (folded column taps) on plain tiles, every other layer on its default tiles
     t1_plain = tmp_path / "t1.json"
-    # (and the output conv: its dedicated kernel folds the column taps too)
-    t1_plain.write_text(json.dumps({key: {**{f"vib{s}.t1": 7 for s in range(3)}, "ref.out": 7}}))
+    # (and the output conv and d3: their dedicated kernels fold the column taps too)
+    t1_plain.write_text(json.dumps({key: {**{f"vib{s}.t1": 7 for s in range(3)}, "ref.out": 7, "ref.d3": 7}}))
     it.autotune(2, str(t1_plain))
     halo = it.run(L, R, ts).cpu().numpy()
     # force every layer onto plain tiles 128 pixels wide through a tile cache entry
@@ -219,13 +219,14 @@ def test_folded_t1_network_matches_plain_t1(torch_cuda, tmp_path):
 
 @pytest.mark.parametrize("H,W,nv", [(71, 399, 2), (64, 512, 3)])
 def test_folded_output_conv_matches_plain(torch_cuda, tmp_path, H, W, nv):
-    """RefineNet's output conv in its dedicated kernel (column taps folded into N, the
-    three taps summed across TMEM lanes, two rows of a 120-pixel strip per tile) against
-    the generic tensor-core conv on plain tiles (a tile width forced for ref.out in the
-    tile cache), the rest of the network unchanged: the two differ only in the FP32 order
-    of the nine taps' sums, so every intermediate is the same and the views agree to far
-    below BF16 noise.  Odd crop height (the last row pair half outside), odd crop width
-    (scalar stores), ragged last strips."""
+    """RefineNet's output conv and d3 in their dedicated kernels (column taps folded into
+    N, the three taps summed across TMEM lanes, tiles walking down 120-pixel strips)
+    against the generic tensor-core convs on plain tiles (a tile width forced for ref.out
+    and ref.d3 in the tile cache), the rest of the network unchanged: the two differ only
+    in the FP32 order of the taps' sums (and d3's bf16 rounding of them), so every
+    earlier intermediate is the same and the views agree to far below BF16 noise.  Odd
+    crop height (the last row pair half outside), odd crop width (scalar stores), ragged
+    last strips."""
     torch = torch_cuda
     left, right = pair(29, H, W, 8.0)
     L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
@@ -234,14 +235,45 @@ def test_folded_output_conv_matches_plain(torch_cuda, tmp_path, H, W, nv):
     folded = it.run(L, R, ts).cpu().numpy()
     blend = it.peek("blend").copy()
     cache = tmp_path / "out.json"
-    cache.write_text(json.dumps({f"{H}x{W} n{nv} p{fvv.FVV_BF16}": {"ref.out": 7}}))
+    cache.write_text(json.dumps({f"{H}x{W} n{nv} p{fvv.FVV_BF16}": {"ref.out": 7, "ref.d3": 7}}))
     it.autotune(nv, str(cache))
     plain = it.run(L, R, ts).cpu().numpy()
     fvv.fvv_interp_status(it.h)
     np.testing.assert_array_equal(it.peek("blend"), blend)
     assert folded.shape == (nv, H, W, 3) and np.isfinite(folded).all()
     d = np.abs(folded - plain)
-    assert d.max() <= 2e-5, float(d.max())
+    assert d.max() <= 2e-3 and d.mean() <= 2e-5, (float(d.max()), float(d.mean()))
+
+
+@pytest.mark.parametrize("H,W,n", [(3, 131, 2), (5, 250, 1)])
+def test_folded_d3_layer_matches_oracle(torch_cuda, H, W, n):
+    """ref.d3 (all-phase transposed conv 64 -> 16, ReLU) in its dedicated kernel (column
+    taps folded into N = 192): bf16 input in the network's 96-channel pixel stride, bf16
+    output of pitch 16, against the oracle's transposed conv of the same bf16-rounded
+    operands (the per-layer bar plus the output's bf16 rounding); ragged strips (131 =
+    120 + 11, 250 = 2 x 120 + 10) and rows walked down each strip."""
+    torch = torch_cuda
+    names = [m[0] for m in weights.manifest()]
+    li = names.index("ref.d3")
+    _, kind, ci, co, _, relu = weights.manifest()[li]
+    assert (kind, ci, co, relu) == ("convT", 64, 16, True)
+    rng = np.random.default_rng(900 + H)
+    x = np.zeros((n, H, W, 96), np.float32)
+    x[..., :ci] = rng.standard_normal((n, H, W, ci)) * 0.5
+    x = _bf16_round(torch, x)
+    wv, bv = weights.layer_views(blob())["ref.d3"]
+    wq = _bf16_round(torch, wv)
+    it = fvv.Interpolator(blob(), 64, 64, precision=fvv.FVV_BF16, max_views=1)
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    out = torch.full((n, 2 * H, 2 * W, co), -7.0, dtype=torch.bfloat16, device="cuda")
+    fvv.fvv_interp_layer(it.h, li, xd, 96, 0, n, H, W, out, co, 0, False)
+    fvv.fvv_interp_status(it.h)
+    got = out.float().cpu().numpy()
+    for i in range(n):
+        ref = oracle.conv_transpose4x4(x[i, ..., :ci], wq, bv, relu=True)
+        scale = max(1.0, float(np.abs(ref).max()))
+        err = np.abs(got[i] - ref) - np.abs(ref) * 2.0 ** -8
+        assert err.max() <= 1e-4 * scale, (i, float(err.max()), scale)
 
 
 @pytest.mark.parametrize("H,W,nv", [(72, 400, 3), (200, 136, 2)])
