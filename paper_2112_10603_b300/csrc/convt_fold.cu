@@ -57,6 +57,7 @@ struct __align__(16) CfBars {
     uint64_t full[kSlots], empty[kSlots];
     uint64_t tmem_full[2], tmem_empty[2];
     uint64_t drain;
+    uint64_t never; // signalled by nothing: the fault-injection wait
     uint32_t tmem_base;
     int abort;
 };
@@ -73,6 +74,7 @@ struct CfParams {
     bf16 *out;                        // 2 h x 2 w x 16 per view (pixel stride 16)
     const int *n_dev;                 // device view count (size-bucket graphs), or NULL
     int n_img, h, w, strips;
+    long long stall_cycles;           // fault injection (tests): > 0 makes the MMA warp wait on `never`
     int *err;
 };
 
@@ -127,6 +129,7 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             ptx::mbar_init(ptx::smem_u32(&bars->tmem_empty[a]), 8); // one arrive per epilogue warp
         }
         ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
+        ptx::mbar_init(ptx::smem_u32(&bars->never), 1);
         bars->abort = 0;
         ptx::fence_barrier_init();
     }
@@ -187,6 +190,9 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
+            // fault injection: a wait that runs out records code 6 and raises the abort flag
+            // before any MMA is issued; the other roles leave, the copies land, TMEM is freed
+            if (p.stall_cycles > 0) wait_bar(ptx::smem_u32(&bars->never), 0, abort, p.err, 6, p.stall_cycles);
             bool ok = wait_bar(ptx::smem_u32(&bars->wfull), 0, abort, p.err, 3);
             ptx::tc_fence_after();
             const uint32_t bw = ptx::smem_u32(sB), sw = ptx::smem_u32(sSlot);
@@ -353,6 +359,7 @@ int tc_convt_fold(fvv_interp *h, int li, const void *in, int in_cs, int N, int h
     p.h = hin; p.w = win;
     p.strips = (win + kTw - 1) / kTw;
     p.err = h->d_err;
+    p.stall_cycles = h->stall_now;
     const long long tiles = (long long)N * p.strips * hin;
     if (tiles > (1ll << 30)) { set_error("too many tiles"); return FVV_ESHAPE; }
     static int sms = 0;
