@@ -134,6 +134,10 @@ static int conv_impl(fvv_interp *h, int li, const void *in, int in_cs, int in_co
         out_conv_ok(h, li, in_cs, N, Hin, Win, epi->crop_h, epi->crop_w))
         return tc_out_conv(h, li, in, N, Hin, Win, epi->ib, epi->final_out_ref, epi->crop_h, epi->crop_w,
                            count_word(h, li), st);
+    // VIBlock t1 with Eq. 2 fused, rows walked down strips (same conditions)
+    if (epi && epi->mode == EPI_RESID && h->tile_force < 0 && h->tile_tw[li] < 0 &&
+        vib_t1_ok(h, li, in_cs, in_coff, N, Hin, Win, out_cs, out_coff, out_f32))
+        return tc_vib_t1(h, li, in, N, Hin, Win, epi->fm_prev, (float *)out, count_word(h, li), st);
     // RefineNet d3 with its column taps folded (same conditions)
     if (!epi && is_bf16(h) && h->tile_force < 0 && h->tile_tw[li] < 0 &&
         convt_fold_ok(h, li, in_cs, in_coff, out_cs, out_coff, out_f32))

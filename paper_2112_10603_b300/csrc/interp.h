@@ -156,6 +156,14 @@ int tc_out_conv(fvv_interp *h, int layer, const void *in, int n, int hp, int wp,
 bool convt_fold_ok(const fvv_interp *h, int layer, int in_cs, int in_coff, int out_cs, int out_coff, bool out_f32);
 int tc_convt_fold(fvv_interp *h, int layer, const void *in, int in_cs, int n, int hin, int win, void *out,
                   const int *n_dev, cudaStream_t st);
+// VIBlock t1 with the Eq. 2 update fused, rows walked down 120-pixel strips
+// (csrc/t1_fold.cu): whether the dedicated kernel takes this call, and its launch
+// (in: n x hin x win x 128 bf16; fm_prev: F^{s-1}, M^{s-1} on the same grid, 5 FP32;
+// out: F^s, M^s, n x 2 hin x 2 win x 5 FP32)
+bool vib_t1_ok(const fvv_interp *h, int layer, int in_cs, int in_coff, int n, int hin, int win, int out_cs,
+               int out_coff, bool out_f32);
+int tc_vib_t1(fvv_interp *h, int layer, const void *in, int n, int hin, int win, const float *fm_prev, float *out,
+              const int *n_dev, cudaStream_t st);
 int tc_stage_conv(fvv_interp *h, int layer, const float4 *imgs, const float *fm_prev, const ViewTab &vt, int nv,
                   int hs, int ws, int circ, void *out, int out_cs, cudaStream_t st);
 bool tc_all_phases(int layer); // transposed conv run as one 3x3 conv over all 4 phases
