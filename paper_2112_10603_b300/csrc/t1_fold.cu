@@ -347,8 +347,10 @@ vib_t1_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             const int f0 = max(0, x0 - 4);
+            // every lane computes (its clamped columns lie in the copied row: lanes 0 and 31
+            // and lanes past the grid read in-range values), only lanes 1..nw store
             float out10[10];
-            if (mine) {
+            {
                 float nb[2][3][5];
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
