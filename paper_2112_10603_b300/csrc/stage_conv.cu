@@ -36,6 +36,10 @@
 
 namespace fvv {
 
+// (csrc/conv_tc.cu) bf16 tensor map, rows of ck_bytes swizzled accordingly
+int tc_encode_map(CUtensorMap *m, int rank, void *base, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
+                  const cuuint32_t *box, int ck_bytes);
+
 namespace {
 
 constexpr int kSt = 126;                                       // output pixels per tile
@@ -166,7 +170,8 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
 
 template <int NG, bool CIRC>
 __global__ void __launch_bounds__(ScCfg<NG>::kThreads, 1)
-stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
+stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmC32,
+                  const __grid_constant__ CUtensorMap tmC30, const ScParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sB = smem;
@@ -195,7 +200,11 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
         ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), 2 * kCo); // two accumulators
         ptx::tmem_relinquish();
     }
-    if (warp == 0 && lane == 0) ptx::prefetch_tmap(&tmB);
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmB);
+        ptx::prefetch_tmap(&tmC32);
+        ptx::prefetch_tmap(&tmC30);
+    }
     if (threadIdx.x >= 64 && threadIdx.x < 64 + kCo) sBias[threadIdx.x - 64] = __ldg(p.bias + threadIdx.x - 64);
     ptx::tc_fence_before();
     __syncthreads();
@@ -276,11 +285,14 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
             }
         }
     } else if (warp < 6) {
-        // ---------------- epilogue: bias, ReLU, bf16 / E4M3, coalesced row stores ----------------
+        // ---------------- epilogue: bias, ReLU, bf16 / E4M3, TMA row stores ----------------
+        // The warp's 32 pixels are staged as 128-byte rows in the tensor maps' 128-byte
+        // swizzle (bf16: two 4 KB boxes, channels 0-63 and 64-127; E4M3: one box) and one
+        // lane stores them with TMA: tmC32 stores 32 pixels, tmC30 the last warp's 30 (the
+        // tile's pixels 126, 127 are the next strip's); the map clips the grid's right edge.
         const int q = warp & 3; // TMEM lanes 32 q .. 32 q + 31 = tile pixels
-        uint8_t *stg = sStg + q * kStgBytes;
-        const uint32_t stg_s = ptx::smem_u32(stg);
-        const uint32_t px_bytes = p.out_fp8 ? kCo : 2 * kCo; // 128 (E4M3) or 256 (bf16)
+        const uint32_t stg_s = ptx::smem_u32(sStg + q * kStgBytes);
+        const CUtensorMap *tmC = q == 3 ? &tmC30 : &tmC32;
         int acc = 0;
         uint32_t acc_phase = 0;
         float vmax = 0.f;
@@ -291,6 +303,9 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
             const bool valid = q * 32 + lane < nvalid;
             if (!warp_wait(ptx::smem_u32(&bars->tmem_full[acc]), acc_phase, abort, p.err, 4)) break;
             ptx::tc_fence_after();
+            // the previous tile's store has read the staging buffer
+            if (lane == 0) ptx::bulk_wait_read<0>();
+            __syncwarp();
             const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * kCo;
 #pragma unroll 1
             for (int c = 0; c < kCo; c += 32) {
@@ -335,7 +350,8 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
                             const uint4 u = make_uint4(
                                 pack_bf16x2(v[8 * hh], v[8 * hh + 1]), pack_bf16x2(v[8 * hh + 2], v[8 * hh + 3]),
                                 pack_bf16x2(v[8 * hh + 4], v[8 * hh + 5]), pack_bf16x2(v[8 * hh + 6], v[8 * hh + 7]));
-                            ptx::st_shared_v4(stg_s + lane * 256 + ((((cb >> 3) + hh) ^ (lane & 7)) << 4), u);
+                            const int ck = (cb >> 3) + hh; // 16-byte chunk 0..15 of the pixel's 256 bytes
+                            ptx::st_shared_v4(stg_s + (ck >> 3) * 4096 + lane * 128 + (((ck & 7) ^ (lane & 7)) << 4), u);
                         }
                     }
                 }
@@ -345,28 +361,17 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const ScParams p) {
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->tmem_empty[acc]));
             if (++acc == 2) { acc = 0; acc_phase ^= 1; }
-            // the warp's valid pixels are consecutive in the output row: 512 bytes per store
-            const int nw = min(max(nvalid - q * 32, 0), 32);
-            uint8_t *dst = (uint8_t *)p.out + (((size_t)n * p.ho + y) * p.wo + x0 + q * 32) * px_bytes;
-            if (p.out_fp8) { // 128-byte pixels: 4 per store, 8 lanes each
-#pragma unroll 4
-                for (int i = 0; i < 8; ++i) {
-                    const int px = i * 4 + (lane >> 3), ch = lane & 7;
-                    if (px < nw)
-                        *reinterpret_cast<uint4 *>(dst + px * 128 + ch * 16) =
-                            *reinterpret_cast<const uint4 *>(stg + px * 128 + ((ch ^ (px & 7)) << 4));
-                }
-            } else { // 256-byte pixels: 2 per store, 16 lanes each
-#pragma unroll 4
-                for (int i = 0; i < 16; ++i) {
-                    const int px = i * 2 + (lane >> 4), ch = lane & 15;
-                    if (px < nw)
-                        *reinterpret_cast<uint4 *>(dst + px * 256 + ch * 16) =
-                            *reinterpret_cast<const uint4 *>(stg + px * 256 + ((ch ^ (px & 7)) << 4));
-                }
+            // generic-proxy staging writes, read by the TMA store (async proxy)
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0 && q * 32 < nvalid) {
+                const int xs = x0 + q * 32;
+                ptx::tma_store_4d(tmC, stg_s, 0, xs, y, n);
+                if (!p.out_fp8) ptx::tma_store_4d(tmC, stg_s + 4096, 64, xs, y, n);
+                ptx::bulk_commit();
             }
-            __syncwarp(); // the staging buffer is rewritten by the next tile
         }
+        if (lane == 0) ptx::bulk_wait<0>(); // the stores have completed before the CTA exits
         if (p.amax && vmax > 0.f) atomicMax(reinterpret_cast<int *>(p.amax), __float_as_int(vmax));
     } else {
         // ---------------- loaders: the stage input, one pixel per thread and row ----------------
@@ -493,8 +498,18 @@ int tc_stage_conv(fvv_interp *h, int li, const float4 *imgs, const float *fm_pre
         FVV_CHECK_CUDA(cudaFuncSetAttribute(stage_conv_kernel<kGroups, true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
     }
+    // output maps: n x ho x wo pixels of 128 channels; E4M3 codes are described as 64
+    // two-byte elements per pixel (a store moves bytes), so both precisions use 128-byte
+    // box rows in the 128-byte swizzle
+    const cuuint64_t pxb = p.out_fp8 ? 128 : 256;
+    cuuint64_t dims[4] = {pxb / 2, (cuuint64_t)p.wo, (cuuint64_t)p.ho, (cuuint64_t)nv};
+    cuuint64_t strides[3] = {pxb, (cuuint64_t)p.wo * pxb, (cuuint64_t)p.ho * p.wo * pxb};
+    cuuint32_t box32[4] = {64, 32, 1, 1}, box30[4] = {64, kSt - 96, 1, 1};
+    CUtensorMap mc32, mc30;
+    FVV_TRY(tc_encode_map(&mc32, 4, out, dims, strides, box32, 128));
+    FVV_TRY(tc_encode_map(&mc30, 4, out, dims, strides, box30, 128));
     const int grid = (int)(tiles < sms ? tiles : sms);
-    kern<<<grid, C::kThreads, C::kSmem, st>>>(*(const CUtensorMap *)h->tc[li].map3, p);
+    kern<<<grid, C::kThreads, C::kSmem, st>>>(*(const CUtensorMap *)h->tc[li].map3, mc32, mc30, p);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());
     return FVV_OK;
