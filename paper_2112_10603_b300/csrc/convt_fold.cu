@@ -21,8 +21,8 @@
 // Warps: 0 issues the copies, 1 allocates TMEM and issues the MMAs, 2-9 are the epilogue:
 // warp 2 + 4 h + q reads TMEM lane quarter q and computes output row 2 y + h (phases
 // 2 h, 2 h + 1): tap sums, bias, ReLU, bf16; its 30 input pixels' 60 output pixels x 32
-// bytes (1920 contiguous bytes of the output row) are staged in shared memory and stored
-// as 16-byte vectors.  Same arithmetic as the generic conv up to the FP32 order of the
+// bytes (1920 contiguous bytes of the output row) are staged in shared memory, two output
+// pixels per 64-byte row in the 64-byte swizzle, and one lane stores them with TMA.  Same arithmetic as the generic conv up to the FP32 order of the
 // three column taps' sums.
 #include <cuda.h>
 
@@ -50,7 +50,9 @@ constexpr int kSlots = 6;                                  // the producer runs 
 constexpr uint32_t kSliceBytes = kN * kRowBytes;           // 24 KB: one folded row-tap slice
 constexpr int kThreads = 320;
 constexpr uint32_t kIdesc = ptx::make_idesc(128, kN, 1, 1);
-constexpr uint32_t kStgBytes = 2 * kWp * kCo * 2;          // per epilogue warp: 60 output pixels x 32 B
+constexpr uint32_t kStgBytes = 2048;                       // per epilogue warp: 60 output pixels x 32 B,
+                                                           // 512-byte aligned (the 64-byte swizzle's span)
+static_assert(kStgBytes >= 2 * kWp * kCo * 2, "d3 staging");
 
 struct __align__(16) CfBars {
     uint64_t wfull;
@@ -67,7 +69,7 @@ constexpr uint32_t kOffStg = kOffSlot + kSlots * kSlotBytes;
 constexpr uint32_t kOffBars = kOffStg + 8 * kStgBytes;
 constexpr size_t kSmem = kOffBars + sizeof(CfBars) + 1024;
 static_assert(kSmem <= 227 * 1024, "folded transposed conv shared memory");
-static_assert(kOffSlot % 1024 == 0 && kOffStg % 16 == 0 && kOffBars % 16 == 0, "folded transposed conv layout");
+static_assert(kOffSlot % 1024 == 0 && kOffStg % 1024 == 0 && kOffBars % 16 == 0, "folded transposed conv layout");
 
 struct CfParams {
     const float *bias;                // 16 output biases
@@ -108,7 +110,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const CfParams p) {
+convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const __grid_constant__ CUtensorMap tmC, const CfParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sB = smem;
@@ -140,6 +143,7 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     if (warp == 0 && lane == 0) {
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
+        ptx::prefetch_tmap(&tmC);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -261,6 +265,9 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             ptx::tc_fence_after();
+            // the previous tile's store has read the staging rows
+            if (lane == 0) ptx::bulk_wait_read<0>();
+            __syncwarp();
             const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256;
             const bool mine = lane >= 1 && lane <= nw;
             // phases 2 hh + px: 16 columns per phase in each column tap's block of 64
@@ -287,7 +294,8 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     v[c] = fmaxf(left + __uint_as_float(rb[c]) + right + bias[c], 0.f); // d3 has ReLU
                 }
                 // output pixel 2 i + px of this lane: 32 bytes = chunks 2 px, 2 px + 1 of the
-                // lane's 64-byte staging row, chunk k stored at k ^ ((lane - 1) >> 1 & 3)
+                // lane's 64-byte staging row, chunk k stored at k ^ ((lane - 1) >> 1 & 3) (the
+                // 64-byte swizzle of a 512-byte-aligned buffer)
                 if (mine) {
                     const int r = lane - 1, key = (r >> 1) & 3;
                     const uint32_t row = stg + r * 64;
@@ -301,22 +309,16 @@ convt_fold_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 }
             }
             if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            // output row 2 y + hh, pixels 2 xw .. 2 xw + 2 nw - 1 = pixel pairs xw .. xw + nw - 1:
+            // one box of 30 pairs x 64 bytes (the map clips the grid's right edge)
+            ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (nw > 0) {
-                // output row 2 y + hh, pixels 2 xw .. 2 xw + 2 nw - 1: 4 nw chunks of 16 bytes
-                uint8_t *dst = (uint8_t *)(p.out + (((size_t)tw.n * (2 * p.h) + 2 * tw.y + hh) * wo + 2 * xw) * kCo);
-                for (int k = lane; k < 4 * nw; k += 32) {
-                    const int r = k >> 2, c = k & 3;
-                    uint4 u;
-                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                                 : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w)
-                                 : "r"(stg + r * 64 + ((c ^ ((r >> 1) & 3)) << 4))
-                                 : "memory");
-                    reinterpret_cast<uint4 *>(dst)[k] = u;
-                }
+            if (lane == 0 && nw > 0) {
+                ptx::tma_store_4d(&tmC, stg, 0, xw, 2 * tw.y + hh, tw.n);
+                ptx::bulk_commit();
             }
-            __syncwarp(); // the staging rows are rewritten by the next tile
         }
+        if (lane == 0) ptx::bulk_wait<0>(); // the stores have completed before the CTA exits
     }
 
     ptx::tc_fence_before();
@@ -369,8 +371,15 @@ int tc_convt_fold(fvv_interp *h, int li, const void *in, int in_cs, int N, int h
         FVV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         FVV_CHECK_CUDA(cudaFuncSetAttribute(convt_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     }
+    // the output: N x 2 hin rows of win pixel pairs (2 x 16 bf16 channels = 64 bytes); boxes
+    // of one row x 30 pairs
+    CUtensorMap mc;
+    cuuint64_t odims[4] = {2 * kCo, (cuuint64_t)win, (cuuint64_t)(2 * hin), (cuuint64_t)N};
+    cuuint64_t ostrides[3] = {4 * kCo, (cuuint64_t)win * 4 * kCo, (cuuint64_t)2 * hin * win * 4 * kCo};
+    cuuint32_t obox[4] = {2 * kCo, kWp, 1, 1};
+    FVV_TRY(tc_encode_map(&mc, 4, out, odims, ostrides, obox, 64));
     const int grid = (int)(tiles < sms ? tiles : sms);
-    convt_fold_kernel<<<grid, kThreads, kSmem, st>>>(ma, *(const CUtensorMap *)h->tc[li].map_k, p);
+    convt_fold_kernel<<<grid, kThreads, kSmem, st>>>(ma, *(const CUtensorMap *)h->tc[li].map_k, mc, p);
     count_launch();
     FVV_CHECK_CUDA(cudaGetLastError());
     return FVV_OK;

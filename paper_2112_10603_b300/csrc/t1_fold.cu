@@ -24,8 +24,8 @@
 // Warps: 0 issues the copies, 1 allocates TMEM and issues the MMAs, 2-9 are the epilogue:
 // warp 2 + 4 h + q reads lane quarter q and writes output row 2 y + h (phases (h, 0),
 // (h, 1)): lanes 1..30 each produce two output pixels x 5 channels; the warp's 60 pixels
-// (1200 contiguous bytes of the output row) are staged in shared memory and stored as
-// 16-byte vectors.
+// (1200 contiguous bytes of the output row) are staged in shared memory and written by one
+// bulk copy (the warp's 30 pixels and the grid's width even; otherwise per-lane stores).
 #include <cuda.h>
 
 #include "interp.h"
@@ -389,6 +389,9 @@ vib_t1_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // output row 2 y + hh, pixels 2 xw .. 2 xw + 2 nw - 1 (5 floats each)
             float *dst = p.out + (((size_t)tw.n * (2 * p.h) + 2 * tw.y + hh) * wo + 2 * xw) * 5;
             if (nw == kWp && (p.w & 1) == 0) {
+                // the previous tile's bulk store has read the staging row
+                if (lane == 0) ptx::bulk_wait_read<0>();
+                __syncwarp();
                 // (lane l - 1's 10 floats at word 10 (l - 1): 2-way bank conflicts)
                 if (mine) {
 #pragma unroll
@@ -396,22 +399,21 @@ vib_t1_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         asm volatile("st.shared.f32 [%0], %1;" ::"r"(stg + (uint32_t)((lane - 1) * 40 + j * 4)), "f"(out10[j])
                                      : "memory");
                 }
+                // 300 floats = 1200 contiguous bytes (the row segment starts 16-byte aligned:
+                // 2 xw x 20 bytes with xw a multiple of 30, rows of 2 w x 20 bytes with w even),
+                // one bulk copy issued by one lane
+                ptx::fence_proxy_async_smem();
                 __syncwarp();
-                // 300 floats = 75 16-byte vectors (the row segment starts 16-byte aligned)
-                for (int k = lane; k < 75; k += 32) {
-                    float4 u;
-                    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                                 : "=f"(u.x), "=f"(u.y), "=f"(u.z), "=f"(u.w)
-                                 : "r"(stg + (uint32_t)k * 16u)
-                                 : "memory");
-                    reinterpret_cast<float4 *>(dst)[k] = u;
+                if (lane == 0) {
+                    ptx::bulk_store(dst, stg, 2 * kWp * 5 * 4);
+                    ptx::bulk_commit();
                 }
-                __syncwarp(); // the staging row is rewritten by the next tile
             } else if (mine) {
 #pragma unroll
                 for (int j = 0; j < 10; ++j) dst[(lane - 1) * 10 + j] = out10[j];
             }
         }
+        if (lane == 0) ptx::bulk_wait<0>(); // the stores have completed before the CTA exits
     }
 
     ptx::tc_fence_before();

@@ -82,6 +82,12 @@ __device__ __forceinline__ void bulk_load(uint32_t sdst, const void *gsrc, uint3
                  "l"(gsrc), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// 1-D bulk copy shared -> global, bulk-group completion (both addresses 16-byte aligned,
+// bytes a multiple of 16)
+__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
 // ---- TMA (tiled, shared -> global, bulk-group completion) -------------------
 __device__ __forceinline__ void tma_store_4d(const void *map, uint32_t src, int c0, int c1, int c2, int c3) {
     asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
