@@ -728,7 +728,7 @@ def main():
             del out
             torch.cuda.empty_cache()
             line["fp8"] = fp8_measure(blob, L, R, ref, out32[mid], args.warmup, args.steps, flush, pk, pk_kind)
-            line["rig"] = rig_measure("bf16", 3, max(10, args.steps), rank)
+            line["rig"] = rig_measure("bf16", 3, max(100, args.steps), rank)   # >= 100 instants
             line["serve"] = serve_measure(args.serve_seconds)
             line["serve_dense"] = serve_dense_measure(args.serve_seconds, "fp8", 3, True)
         print(json.dumps(line), flush=True)
