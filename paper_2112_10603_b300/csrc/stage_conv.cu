@@ -378,9 +378,14 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant
         // group g computes the new input rows of the CTA's tiles g, g + NG, ...: the two rows
         // of a continuing tile together (their gathers in flight at once), plus row 2y - 1
         // where a tile starts a strip segment
-        const int g = (warp - 6) / 8, gt = ((warp - 6) % 8) * 32 + lane;
-        const int i = gt + 1;               // slot pixel of this thread (1 .. 253 feed the tile)
-        const int pr = i >> 1, half = i & 1; // slot row, even / odd pixel of the row's pair
+        // Warp w of a group covers slot pixels 32 w .. 32 w + 31; lane l takes pair row
+        // 16 w + (l & 7) + 8 (l >> 4), pixel (l >> 3) & 1 of the pair, so that the 8 lanes of
+        // each quarter-warp store phase write 8 consecutive pair rows: 8 distinct 16-byte
+        // chunks of the 128-byte swizzle, no bank conflicts (consecutive pixels per lane
+        // put two rows 4 apart on the same chunk).  Pixels 1 .. 253 feed the tile.
+        const int g = (warp - 6) / 8, w8 = (warp - 6) % 8;
+        const int pr = 16 * w8 + (lane & 7) + 8 * (lane >> 4), half = (lane >> 3) & 1; // slot row, pixel of its pair
+        const int i = 2 * pr + half;        // slot pixel of this thread
         const uint32_t slot0 = ptx::smem_u32(sSlot) + pr * 128;
         bool stop = false;
         auto put = [&](int slot, const uint4 (&cv)[3], bool inside) {
@@ -405,7 +410,7 @@ stage_conv_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant
             for (int j = 0; j < nr && !stop; ++j)
                 stop = !warp_wait(ptx::smem_u32(&bars->empty[rg[j].slot]), rg[j].par ^ 1u, abort, p.err, 1);
             if (stop) break;
-            if (i <= kNeed) {
+            if (i >= 1 && i <= kNeed) {
                 // rows Y = 2y + rr - 1 for rr = 3 - nr .. 2; outside the grid: zeros (zero
                 // padding) computed from clamped coordinates, or wrapped (circular)
                 const int X0 = 2 * x0 - 2 + i;
