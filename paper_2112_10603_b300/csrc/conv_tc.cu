@@ -126,7 +126,7 @@ __device__ __forceinline__ uint8_t to_e4m3(float v) {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
-struct __align__(8) Bars {
+struct __align__(16) Bars { // (16: the staged biases that follow it are read as float4)
     uint64_t full[16], empty[16], tmem_full[2], tmem_empty[2], drain;
     uint64_t never; // signalled by nothing: the fault-injection wait
     uint32_t tmem_base;
@@ -214,6 +214,32 @@ template <bool SB> __device__ __forceinline__ float bias_of(const TcParams &p, u
 }
 template <bool SB> __device__ __forceinline__ float scale_of(const TcParams &p, uint32_t ss, int co) {
     return SB ? ptx::lds_f32(ss + 4 * co) : (p.acc_scale ? __ldg(p.acc_scale + co) : 1.f);
+}
+// Biases and scales of 16 consecutive output channels co0 .. co0 + 15 (co0 a multiple of
+// 16): from the staged copies as four 16-byte broadcast loads each (SB), the scales only
+// for E4M3 layers (F8; 1 without); else through the scalar paths above.
+template <bool SB, int F8>
+__device__ __forceinline__ void bias_scale16(const TcParams &p, uint32_t sb, uint32_t ss, int co0, float (&b)[16],
+                                             float (&sc)[16]) {
+    if (SB) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = ptx::lds_v4f(sb + 4 * (co0 + 4 * k));
+            b[4 * k] = v.x; b[4 * k + 1] = v.y; b[4 * k + 2] = v.z; b[4 * k + 3] = v.w;
+            if (F8) {
+                const float4 w = ptx::lds_v4f(ss + 4 * (co0 + 4 * k));
+                sc[4 * k] = w.x; sc[4 * k + 1] = w.y; sc[4 * k + 2] = w.z; sc[4 * k + 3] = w.w;
+            } else {
+                sc[4 * k] = sc[4 * k + 1] = sc[4 * k + 2] = sc[4 * k + 3] = 1.f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            b[j] = bias_of<SB>(p, sb, co0 + j);
+            sc[j] = scale_of<SB>(p, ss, co0 + j);
+        }
+    }
 }
 template <bool SB>
 __device__ __forceinline__ void resid_store(const TcParams &p, uint32_t sb, uint32_t ss, const float (&nb)[3][3][5],
@@ -961,11 +987,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     // bias, ReLU, conversion and swizzled staging of columns c .. c + 15
                     // (output channels cc .. cc + 15)
                     auto stage16 = [&](int c, int cc, const uint32_t(&r)[16]) {
-                        float v[16];
+                        float v[16], bq[16], sq[16];
+                        bias_scale16<SB, F8>(p, sbias, sscale, cc, bq, sq);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, cc + j) +
-                                      bias_of<SB>(p, sbias, cc + j);
+                            float a = __uint_as_float(r[j]) * sq[j] + bq[j];
                             v[j] = p.relu ? fmaxf(a, 0.f) : a;
                         }
                         if (p.amax && valid) { // calibration only
@@ -1069,12 +1095,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     continue;
                 }
-                if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co) {
-                    float v[16];
+                if (p.epi.mode == EPI_STORE && !p.out_f32 && p.vec_ok && co0 + 16 <= p.co && (co0 & 3) == 0) {
+                    float v[16], bq[16], sq[16];
+                    bias_scale16<SB, F8>(p, sbias, sscale, co0, bq, sq);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        float a = __uint_as_float(r[j]) * scale_of<SB>(p, sscale, co0 + j) +
-                                  bias_of<SB>(p, sbias, co0 + j);
+                        float a = __uint_as_float(r[j]) * sq[j] + bq[j];
                         v[j] = p.relu ? fmaxf(a, 0.f) : a;
                     }
                     if (p.amax) { // calibration only

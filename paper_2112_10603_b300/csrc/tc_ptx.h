@@ -118,6 +118,12 @@ __device__ __forceinline__ float lds_f32(uint32_t addr) {
     asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
     return v;
 }
+// read-only shared-memory float4 (16-byte aligned address)
+__device__ __forceinline__ float4 lds_v4f(uint32_t addr) {
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
 __device__ __forceinline__ void prefetch_tmap(const void *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
