@@ -1,0 +1,69 @@
+"""3840 x 2160, the largest resolution of the serving mix, on the tensor-core path.
+
+One FP64 oracle view at this size takes minutes on the host cores, so the full-size
+launch configurations (tile counts of every layer, the grids of the gather kernels, the
+index arithmetic at 4x the 1080p pixel count) are checked through properties that hold
+at any size, each pinned elsewhere against the oracle at sizes it finishes in seconds:
+
+* the BF16 views against the plain FP32 path (itself within 1e-4 of the oracle at 256^2
+  and 1080p) at the BF16 bar, 45 dB, every value finite and in [0, 1];
+* a view computed alone equals the same view inside the batch, bit for bit;
+* circular padding: shifting both frames cyclically by multiples of 16 pixels shifts
+  the view bit for bit.
+"""
+import numpy as np
+import pytest
+
+import paper_2112_10603_b300 as fvv
+from tests.gpu_common import blob, pair, psnr
+
+pytestmark = pytest.mark.gpu
+
+H, W = 2160, 3840
+DISP = 128.0   # the 1080p workload's 64 pixels of disparity at twice the resolution
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2112_10603_b300 import build as fvv_build
+    fvv_build.build()
+    return torch
+
+
+def test_2160p_bf16_vs_fp32_and_alone(torch_cuda):
+    torch = torch_cuda
+    left, right = pair(21, H, W, DISP)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ts = [0.25, 0.625]
+    bf = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=2)
+    out_b = bf.run(L, R, ts).cpu().numpy()
+    alone = bf.run(L, R, ts[1:]).cpu().numpy()
+    fvv.fvv_interp_status(bf.h)
+    bf.close()
+    fp = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP32, max_views=2)
+    out_f = fp.run(L, R, ts).cpu().numpy()
+    fvv.fvv_interp_status(fp.h)
+    fp.close()
+    for out in (out_b, out_f):
+        assert np.isfinite(out).all()
+        assert out.min() >= 0.0 and out.max() <= 1.0
+    for v in range(len(ts)):
+        assert psnr(out_b[v], out_f[v]) >= 45.0, (v, psnr(out_b[v], out_f[v]))
+    np.testing.assert_array_equal(alone[0], out_b[1])
+
+
+def test_2160p_bf16_circular_shift_equivariance(torch_cuda):
+    torch = torch_cuda
+    left, right = pair(22, H, W, DISP)
+    shift = (48, -160)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=1, pad_mode=fvv.FVV_PAD_CIRCULAR)
+    a = it.run(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), [0.5]).cpu().numpy()[0]
+    Ls = torch.from_numpy(np.ascontiguousarray(np.roll(left, shift, (0, 1)))).cuda()
+    Rs = torch.from_numpy(np.ascontiguousarray(np.roll(right, shift, (0, 1)))).cuda()
+    b = it.run(Ls, Rs, [0.5]).cpu().numpy()[0]
+    fvv.fvv_interp_status(it.h)
+    it.close()
+    assert np.isfinite(a).all()
+    np.testing.assert_array_equal(np.roll(a, shift, (0, 1)), b)

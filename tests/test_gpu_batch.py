@@ -84,6 +84,40 @@ def test_rig_instant_uneven_counts(torch_cuda):
         np.testing.assert_array_equal(out[offs[p]:offs[p + 1]], ref)
 
 
+def test_rig_instant_with_an_empty_pair(torch_cuda):
+    """A rig instant in which one pair asks for no views (view_offsets repeats an entry):
+    the other pairs' views equal per-pair runs bit for bit and the FP64 oracle's views
+    within 1e-4 (FP32 path); a call with no views at all is refused (FVV_ESHAPE)."""
+    torch = torch_cuda
+    H, W = 40, 72
+    frames = scene.rig(17, H, W, n_cams=5, max_disp=6.0)
+    cams = [torch.from_numpy(c).cuda() for c in frames]
+    counts = [2, 0, 1, 2]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    ts = np.array([0.3, 0.8, 0.5, 0.1, 0.9], np.float32)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP32, max_views=8, max_cams=5)
+    out = it.run_batch(cams, [0, 1, 2, 3], offs, ts).cpu().numpy()
+    one = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP32, max_views=4)
+    for p in range(4):
+        if counts[p] == 0:
+            continue
+        ref = one.run(cams[p], cams[p + 1], ts[offs[p]:offs[p + 1]]).cpu().numpy()
+        np.testing.assert_array_equal(out[offs[p]:offs[p + 1]], ref)
+        for v in range(offs[p], offs[p + 1]):
+            o = oracle.vinet_forward(blob(), frames[p], frames[p + 1], float(ts[v]))
+            assert float(np.abs(out[v] - o).max()) <= 1e-4, v
+    dev_out = torch.empty((1, H, W, 3), device="cuda")
+    with pytest.raises(fvv.FvvError) as e:
+        it.run_batch(cams, [0, 1], np.array([0, 0, 0]), np.zeros(1, np.float32), out=dev_out)
+    assert e.value.code == fvv.FVV_ESHAPE
+    with pytest.raises(fvv.FvvError) as e:
+        fvv.fvv_interp_run(it.h, cams[0], cams[1], np.zeros(1, np.float32), 0, dev_out)
+    assert e.value.code == fvv.FVV_ESHAPE
+    fvv.fvv_interp_status(it.h)
+    it.close()
+    one.close()
+
+
 def test_rig_instant_matches_oracle(torch_cuda):
     """A batched rig instant (4 pairs of a 5-camera arc, uneven view counts, random t)
     against the FP64 oracle, view by view, on the FP32 and the BF16 path."""
