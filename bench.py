@@ -332,6 +332,16 @@ def serve_measure(seconds, sweep=False):
             "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "max_ms": main["max_ms"],
             "offered_req_per_s": main["offered_req_per_s"], "superseded_frac": main["superseded_frac"],
             "rejected": main["rejected"], "device_gib": st["device_bytes"] / 2 ** 30}
+    # the offered load against what the server completes, in 1080p-equivalent views (pixels
+    # relative to 1920x1080, at the offered resolution mix): an open-loop load beyond the
+    # completion rate queues until latest-wins supersedes the backlog, so p99 is then
+    # queueing time, not render time
+    px = sum(m * h * w / (1080 * 1920) for m, (h, w) in zip(SERVE_MIX, SERVE_RES))
+    line["offered_1080p_equiv_views_per_s"] = main["offered_req_per_s"] * px
+    line["completed_1080p_equiv_views_per_s"] = main["completed_views_per_s"] * px
+    line["note"] = ("on demand: the offered load is %.1fx the completion rate, so requests queue and "
+                    "latest-wins supersedes them; serve_dense answers at once from the newest "
+                    "complete per-instant view set" % (main["offered_req_per_s"] / max(main["completed_views_per_s"], 1e-9)))
     if users_sweep is not None:
         line["users_sweep"] = users_sweep
     return line
