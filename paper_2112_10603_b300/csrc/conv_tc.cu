@@ -1183,6 +1183,7 @@ int get_encoder() {
 }
 
 bool g_encode_u8 = false; // next encode() describes 1-byte (FP8) elements
+bool g_encode_l2_64 = false; // next encode() asks for 64-byte L2 fills (instead of 256)
 
 CUtensorMapSwizzle swz_for(int ck_bytes) {
     return ck_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -1194,7 +1195,8 @@ int encode(CUtensorMap *m, int rank, void *base, const cuuint64_t *dims, const c
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = g_encode(m, g_encode_u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, base,
                           dims, strides_bytes, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz_for(ck_bytes), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz_for(ck_bytes),
+                          g_encode_l2_64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d), rank %d", (int)r, rank);
@@ -1852,7 +1854,11 @@ int tc_conv(fvv_interp *h, int li, const void *in, int in_cs, int in_coff, int N
             rc = encode(&ma, 5, (void *)in, dims, strides, box, 2 * ck * es);
         } else {
             cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)tw_, 1, (cuuint32_t)th_, 1};
+            // a channel slice of wider pixels (RefineNet's stride-2 encoders read their
+            // level's slots): 64-byte L2 fills, so the unread channels are not fetched
+            g_encode_l2_64 = in_cs > cip;
             rc = encode(&ma, 5, (void *)in, dims, strides, box, ck * es);
+            g_encode_l2_64 = false;
         }
     } else {
         cuuint64_t dims[4] = {(cuuint64_t)in_cs, (cuuint64_t)Wm, (cuuint64_t)Hm, (cuuint64_t)N};
