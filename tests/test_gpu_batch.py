@@ -84,6 +84,28 @@ def test_rig_instant_uneven_counts(torch_cuda):
         np.testing.assert_array_equal(out[offs[p]:offs[p + 1]], ref)
 
 
+def test_rig_1080p_batch_equals_per_pair_runs(torch_cuda):
+    """The rig configuration's launch shape: 1920 x 1080 frames of a 4-camera arc, three
+    pairs with uneven view counts in one batched call (BF16, graph replay) equal the
+    per-pair calls bit for bit (every layer's per-pixel arithmetic is the same whatever
+    the batch and its size bucket)."""
+    torch = torch_cuda
+    H, W = 1080, 1920
+    cams = [torch.from_numpy(c).cuda() for c in scene.rig(4, H, W, n_cams=4, max_disp=64.0)]
+    counts = [3, 1, 2]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    ts = np.array([0.2, 0.5, 0.9, 0.4, 0.1, 0.7], np.float32)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=6, max_cams=4)
+    out = it.run_batch(cams, [0, 1, 2], offs, ts).cpu().numpy()
+    fvv.fvv_interp_status(it.h)
+    it.close()
+    one = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_BF16, max_views=3)
+    for p in range(3):
+        ref = one.run(cams[p], cams[p + 1], ts[offs[p]:offs[p + 1]]).cpu().numpy()
+        np.testing.assert_array_equal(out[offs[p]:offs[p + 1]], ref)
+    one.close()
+
+
 def test_rig_instant_with_an_empty_pair(torch_cuda):
     """A rig instant in which one pair asks for no views (view_offsets repeats an entry):
     the other pairs' views equal per-pair runs bit for bit and the FP64 oracle's views
