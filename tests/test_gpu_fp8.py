@@ -21,6 +21,11 @@ pytestmark = pytest.mark.gpu
 # image gradient of the 1080p ones, so the same flow error costs ~6 dB more there
 # (1080p: 40.7 dB, held to the 38 dB target below).
 PSNR_FP8_FLOOR = 34.0
+# Circular padding, same scenes: 32.8-32.9 dB.  The stage flows carry the same relative
+# error (0.09-0.13); the loss is at the wrapped seams, where the non-periodic scene's
+# opposite edges meet (mean error in the 4 border pixels 0.038-0.041 against 0.010-0.012
+# with zero padding, interior 0.014 against 0.012; BF16 loses ~1 dB there too).
+PSNR_FP8_CIRC_FLOOR = 32.0
 FLOW_REL_ERR_MAX = 0.14   # RMS flow error / RMS flow, each stage s of Eq. 2
 
 
@@ -169,3 +174,34 @@ def test_fp8_1080p_fifteen_views(torch_cuda):
         assert rel <= FLOW_REL_ERR_MAX, (s, rel)
     alone = it.run(L, R, [ts[3]]).cpu().numpy()
     np.testing.assert_array_equal(alone[0], out[3])
+
+
+def test_fp8_circular_mode_and_shift_equivariance(torch_cuda):
+    """E4M3 layers with circular padding (the wrapped-border copies of every conv input
+    feed the E4M3 kernels as they feed the BF16 ones; calibration runs in the same mode):
+    the view against the circular FP64 oracle at this size's circular FP8 floor, the stage flows
+    within the same relative error bound, and shifting both frames cyclically by multiples
+    of 16 pixels shifts the view bit for bit (the scales are fixed by calibration, so every
+    element's arithmetic is the same wherever it lies)."""
+    torch = torch_cuda
+    H, W, seed, disp = 256, 256, 1, 12.0
+    left, right = pair(seed, H, W, disp)
+    ref, d = oracle_view(seed, H, W, disp, 0.5, circ=True)
+    it = fvv.Interpolator(blob(), H, W, precision=fvv.FVV_FP8, max_views=1, pad_mode=fvv.FVV_PAD_CIRCULAR)
+    fvv.fvv_calibrate_fp8(it.h, _calib_frames(torch, H, W), 2)
+    a = it.run(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), [0.5]).cpu().numpy()[0]
+    p = psnr(a, ref)
+    print(f"FP8 circular {H}x{W}: PSNR {p:.2f} dB vs FP64")
+    assert np.isfinite(a).all() and a.min() >= 0 and a.max() <= 1
+    assert p >= PSNR_FP8_CIRC_FLOOR, p
+    for s in range(3):
+        g, r = it.peek(f"vib{s}")[..., :4], d[f"vib{s}"][..., :4]
+        rel = np.sqrt(((g - r) ** 2).mean() / (r ** 2).mean())
+        assert rel <= FLOW_REL_ERR_MAX, (s, rel)
+    shift = (32, -80)
+    Ls = torch.from_numpy(np.ascontiguousarray(np.roll(left, shift, (0, 1)))).cuda()
+    Rs = torch.from_numpy(np.ascontiguousarray(np.roll(right, shift, (0, 1)))).cuda()
+    b = it.run(Ls, Rs, [0.5]).cpu().numpy()[0]
+    fvv.fvv_interp_status(it.h)
+    it.close()
+    np.testing.assert_array_equal(np.roll(a, shift, (0, 1)), b)
